@@ -1,0 +1,372 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics,
+independent of the oracle's own code paths (closed forms, quadrature,
+identities, brute force).  None of these needs a GPU."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import molgen
+import oracle
+
+
+def cart_list(l):
+    return [(x, y, l - x - y) for x in range(l, -1, -1) for y in range(l - x, -1, -1)]
+
+
+# --------------------------------------------------------------------------
+# Boys function (Eq. boys-fn-def)
+# --------------------------------------------------------------------------
+
+def test_boys_at_zero():
+    F = oracle.boys(18, 0.0)
+    assert np.allclose(F, [1.0 / (2 * m + 1) for m in range(19)], rtol=1e-15, atol=0)
+
+
+def test_boys_f0_erf_closed_form():
+    for T in np.concatenate([np.linspace(1e-6, 2, 17), np.linspace(2, 120, 41)]):
+        ref = 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))
+        assert abs(oracle.boys(0, T)[0] - ref) <= 2e-15 * ref
+
+
+def test_boys_gauss_legendre_quadrature(rng):
+    """int_0^1 t^{2m} exp(-T t^2) dt by composite Gauss-Legendre (8 panels x 32
+    points, 256 nodes; a single 200-node rule carries ~1e-13 node errors)."""
+    x, w = np.polynomial.legendre.leggauss(32)
+    t = np.concatenate([(k + 0.5 * (x + 1.0)) / 8 for k in range(8)])
+    w = np.concatenate([w / 16] * 8)
+    for _ in range(400):
+        m = int(rng.integers(0, 19))
+        T = float(rng.choice([rng.uniform(0, 1), rng.uniform(1, 40), rng.uniform(40, 120)]))
+        ref = np.sum(w * t ** (2 * m) * np.exp(-T * t * t))
+        F = oracle.boys(m, T)[m]
+        assert abs(F - ref) <= 1e-13 * ref, (m, T, F, ref)
+
+
+def test_boys_downward_recurrence_identity(rng):
+    for _ in range(100):
+        T = float(rng.uniform(0, 100))
+        F = oracle.boys(12, T)
+        for m in range(12):
+            lhs = (2 * m + 1) * F[m]
+            rhs = 2 * T * F[m + 1] + math.exp(-T)
+            assert abs(lhs - rhs) <= 1e-14 * lhs
+
+
+# --------------------------------------------------------------------------
+# normalisation (Sec. 2.1): every Cartesian function has unit self-overlap
+# --------------------------------------------------------------------------
+
+def test_overlap_diagonal_is_one():
+    p = molgen.problem(0)
+    S = oracle.overlap(p.basis)
+    assert np.abs(np.diag(S) - 1).max() < 1e-14
+    assert np.abs(S - S.T).max() < 1e-14
+    # Gram matrix of linearly independent functions is positive definite
+    assert np.linalg.eigvalsh(S).min() > 0
+
+
+def test_overlap_two_s_closed_form(rng):
+    """<s_A|s_B> = (4ab/(a+b)^2)^(3/4) exp(-ab/(a+b) R^2) for normalised primitives."""
+    for _ in range(20):
+        a, b = rng.uniform(0.1, 20, 2)
+        A, B = rng.uniform(-2, 2, (2, 3))
+        bas = molgen.single_shell_basis([(0, A, [a], [1.0]), (0, B, [b], [1.0])])
+        S = oracle.overlap(bas)
+        ref = (4 * a * b / (a + b) ** 2) ** 0.75 * math.exp(-a * b / (a + b) * np.sum((A - B) ** 2))
+        assert abs(S[0, 1] - ref) <= 1e-14
+
+
+# --------------------------------------------------------------------------
+# ERIs
+# --------------------------------------------------------------------------
+
+def test_ssss_closed_form(rng):
+    """[ss|ss] = 2 pi^{5/2} / (p q sqrt(p+q)) K_AB K_CD F_0(T) (unit primitives)."""
+    for _ in range(200):
+        a, b, c, d = rng.uniform(0.05, 50, 4)
+        A, B, C, D = rng.uniform(-3, 3, (4, 3))
+        p, q = a + b, c + d
+        P, Q = (a * A + b * B) / p, (c * C + d * D) / q
+        T = p * q / (p + q) * np.sum((P - Q) ** 2)
+        F0 = 1.0 if T == 0 else 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))
+        ref = 2 * math.pi ** 2.5 / (p * q * math.sqrt(p + q)) * math.exp(
+            -a * b / p * np.sum((A - B) ** 2) - c * d / q * np.sum((C - D) ** 2)) * F0
+        v = oracle.prim_eri(0, 0, 0, 0, a, A, b, B, c, C, d, D)[0, 0, 0, 0]
+        assert abs(v - ref) <= 1e-13 * abs(ref) + 1e-250, (v, ref)
+
+
+def test_single_s_self_repulsion():
+    """A normalised s Gaussian of exponent a: (ss|ss) = 2 sqrt(a/pi); a one-shell
+    basis then has J_00 = K_00 = (ss|ss) D_00."""
+    for a in (0.3, 1.0, 7.5):
+        bas = molgen.single_shell_basis([(0, [0.1, -0.2, 0.3], [a], [1.0])])
+        v = oracle.shell_eri(bas, 0, 0, 0, 0)[0, 0, 0, 0]
+        assert abs(v - 2 * math.sqrt(a / math.pi)) < 1e-14
+        D = np.array([[0.7]])
+        J, K = oracle.jk(bas, D, tau=0.0, mode=oracle.SCREEN_NONE, eps_prune=0.0)
+        assert abs(J[0, 0] - v * 0.7) < 1e-14 and abs(K[0, 0] - v * 0.7) < 1e-14
+
+
+def _quadrature_eri(la, lb, lc, ld, a, A, b, B, c, C, d, D, nt=400):
+    """Brute force: 1/r12 = 2/sqrt(pi) int_0^inf exp(-t^2 r12^2) dt; for fixed t
+    the 6-D integral factorises into three 2-D Gaussian moments, done exactly
+    with 2-D Gauss-Hermite in the eigenbasis of the quadratic form."""
+    p, q = a + b, c + d
+    P, Q = (a * A + b * B) / p, (c * C + d * D) / q
+    pref = math.exp(-a * b / p * np.sum((A - B) ** 2) - c * d / q * np.sum((C - D) ** 2))
+    gx, gw = np.polynomial.hermite.hermgauss(12)
+    Y1, Y2 = np.meshgrid(gx, gx, indexing="ij")
+    W = np.outer(gw, gw)
+    scale = math.sqrt(p * q / (p + q))
+    s, ws = np.polynomial.legendre.leggauss(nt)
+    s = 0.5 * (s + 1)
+    ws = 0.5 * ws
+    ts = scale * s / (1 - s)
+    dts = scale / (1 - s) ** 2
+    la_c, lb_c, lc_c, ld_c = (cart_list(l) for l in (la, lb, lc, ld))
+    out = np.zeros((len(la_c), len(lb_c), len(lc_c), len(ld_c)))
+    # per t, per axis, moments M[ax][i][j][k][m] = int int (x1-A)^i (x1-B)^j (x2-C)^k (x2-D)^m e^{-Q}
+    acc = np.zeros_like(out)
+    for t, wt, dt in zip(ts, ws, dts):
+        mom = []
+        for ax in range(3):
+            # quadratic form p(x1-P)^2 + q(x2-Q)^2 + t^2 (x1-x2)^2
+            M = np.array([[p + t * t, -t * t], [-t * t, q + t * t]])
+            rhs = np.array([p * P[ax], q * Q[ax]])
+            m0 = np.linalg.solve(M, rhs)
+            c0 = p * P[ax] ** 2 + q * Q[ax] ** 2 - rhs @ m0
+            lam, V = np.linalg.eigh(M)
+            X1 = m0[0] + V[0, 0] * Y1 / math.sqrt(lam[0]) + V[0, 1] * Y2 / math.sqrt(lam[1])
+            X2 = m0[1] + V[1, 0] * Y1 / math.sqrt(lam[0]) + V[1, 1] * Y2 / math.sqrt(lam[1])
+            jac = math.exp(-c0) / math.sqrt(lam[0] * lam[1])
+            mm = {}
+            for i in range(la + 1):
+                for j in range(lb + 1):
+                    for k in range(lc + 1):
+                        for m in range(ld + 1):
+                            f = (X1 - A[ax]) ** i * (X1 - B[ax]) ** j * (X2 - C[ax]) ** k * (X2 - D[ax]) ** m
+                            mm[(i, j, k, m)] = jac * np.sum(W * f)
+            mom.append(mm)
+        for ia, u in enumerate(la_c):
+            for ib, v in enumerate(lb_c):
+                for ic, w_ in enumerate(lc_c):
+                    for id_, z in enumerate(ld_c):
+                        val = 1.0
+                        for ax in range(3):
+                            val *= mom[ax][(u[ax], v[ax], w_[ax], z[ax])]
+                        acc[ia, ib, ic, id_] += wt * dt * val
+    return pref * 2 / math.sqrt(math.pi) * acc
+
+
+@pytest.mark.parametrize("ls", [(0, 0, 0, 0), (1, 0, 0, 0), (1, 1, 0, 0), (1, 0, 1, 0), (1, 1, 1, 1),
+                                (2, 0, 1, 0), (2, 1, 2, 0), (2, 2, 1, 1), (2, 2, 2, 2), (3, 0, 1, 0),
+                                (3, 1, 2, 0), (3, 3, 0, 0)])
+def test_eri_brute_force_quadrature(ls, rng):
+    la, lb, lc, ld = ls
+    a, b, c, d = rng.uniform(0.3, 3.0, 4)
+    A, B, C, D = rng.uniform(-1.0, 1.0, (4, 3))
+    ref = _quadrature_eri(la, lb, lc, ld, a, A, b, B, c, C, d, D)
+    val = oracle.prim_eri(la, lb, lc, ld, a, A, b, B, c, C, d, D)
+    err = np.abs(val - ref).max() / np.abs(ref).max()
+    assert err < 1e-11, err
+
+
+def test_centre_derivative_identity(rng):
+    """d/dA_x [a b|c d] = 2 alpha [a+1_x b|c d] - a_x [a-1_x b|c d] (Sec. 2.1)."""
+    for la, lb, lc, ld in [(0, 1, 1, 0), (1, 1, 0, 1), (2, 1, 1, 0), (2, 2, 1, 1), (3, 1, 2, 0), (3, 2, 3, 3)]:
+        a, b, c, d = rng.uniform(0.3, 2.0, 4)
+        A, B, C, D = rng.uniform(-1.0, 1.0, (4, 3))
+        up = oracle.prim_eri(la + 1, lb, lc, ld, a, A, b, B, c, C, d, D)
+        dn = oracle.prim_eri(la - 1, lb, lc, ld, a, A, b, B, c, C, d, D) if la > 0 else None
+        h = 1e-3
+        for ax in range(3):
+            def f(delta):
+                A2 = A.copy()
+                A2[ax] += delta
+                return oracle.prim_eri(la, lb, lc, ld, a, A2, b, B, c, C, d, D)
+            fd = (-f(2 * h) + 8 * f(h) - 8 * f(-h) + f(-2 * h)) / (12 * h)
+            comps = cart_list(la)
+            up_c, dn_c = cart_list(la + 1), cart_list(la - 1) if la > 0 else []
+            for ia, u in enumerate(comps):
+                uu = list(u)
+                uu[ax] += 1
+                ana = 2 * a * up[up_c.index(tuple(uu))]
+                if u[ax] > 0:
+                    ud = list(u)
+                    ud[ax] -= 1
+                    ana = ana - u[ax] * dn[dn_c.index(tuple(ud))]
+                scale = max(np.abs(ana).max(), 1e-3)
+                assert np.abs(fd[ia] - ana).max() <= 1e-7 * scale, (ls, ax, ia)
+
+
+def test_eightfold_symmetry(rng):
+    bas = molgen.random_shells(rng, [0, 1, 2, 3, 1, 2], spread=1.2)
+    for a, b, c, d in [(1, 2, 3, 4), (3, 0, 5, 2), (2, 2, 1, 5), (3, 3, 3, 3), (5, 4, 2, 1)]:
+        e = oracle.shell_eri(bas, a, b, c, d)
+        ref = np.abs(e).max()
+        perms = [((b, a, c, d), (1, 0, 2, 3)), ((a, b, d, c), (0, 1, 3, 2)), ((b, a, d, c), (1, 0, 3, 2)),
+                 ((c, d, a, b), (2, 3, 0, 1)), ((d, c, a, b), (3, 2, 0, 1)), ((c, d, b, a), (2, 3, 1, 0)),
+                 ((d, c, b, a), (3, 2, 1, 0))]
+        for (s0, s1, s2, s3), axes in perms:
+            e2 = oracle.shell_eri(bas, s0, s1, s2, s3)
+            # e2[i0,i1,i2,i3] with i_k the component of shell s_k; map back
+            back = np.transpose(e2, np.argsort(axes))
+            assert np.abs(back - e).max() <= 5e-14 * ref
+
+
+def test_schwarz_inequality(rng):
+    bas = molgen.random_shells(rng, [0, 1, 2, 3, 0, 1, 2], spread=2.0)
+    G, Gp = oracle.schwarz(bas)
+    ns = len(bas["l"])
+    for _ in range(40):
+        a, b, c, d = rng.integers(0, ns, 4)
+        e = oracle.shell_eri(bas, a, b, c, d)
+        assert np.abs(e).max() <= G[a, b] * G[c, d] * (1 + 1e-12)
+    # diagonal element (mn|mn) = G^2 for the maximising pair
+    for a, b in [(0, 1), (2, 3), (4, 6)]:
+        e = oracle.shell_eri(bas, a, b, a, b)
+        n = e.shape[0] * e.shape[1]
+        diag = np.diag(e.reshape(n, n))
+        assert abs(math.sqrt(diag.max()) - G[a, b]) <= 1e-13 * G[a, b]
+        assert G[a, b] == G[b, a]
+
+
+def test_translation_invariance(rng):
+    bas = molgen.random_shells(rng, [1, 2, 0, 3, 2], spread=1.5)
+    shift = rng.uniform(-5, 5, 3)
+    bas2 = dict(bas)
+    bas2["center"] = bas["center"] + shift
+    for q in [(0, 1, 2, 3), (4, 3, 1, 0), (1, 1, 4, 2)]:
+        e1, e2 = oracle.shell_eri(bas, *q), oracle.shell_eri(bas2, *q)
+        assert np.abs(e1 - e2).max() <= 1e-13 * np.abs(e1).max()
+
+
+def test_rotation_covariance_sp(rng):
+    """s functions are invariant and p functions rotate as vectors, so J and K
+    of the rotated molecule equal T J T^T for the rotated density T D T^T."""
+    bas = molgen.random_shells(rng, [0, 1, 1, 0, 1], spread=1.5)
+    Rm = molgen.random_rotation(rng)
+    bas2 = dict(bas)
+    bas2["center"] = bas["center"] @ Rm.T
+    n = oracle.nbf(bas)
+    T = np.zeros((n, n))
+    o = 0
+    for l in bas["l"]:
+        if l == 0:
+            T[o, o] = 1.0
+        else:
+            T[o:o + 3, o:o + 3] = Rm
+        o += oracle.ncart(int(l))
+    D = rng.uniform(-1, 1, (n, n))
+    D = D + D.T
+    J, K = oracle.jk(bas, D, mode=oracle.SCREEN_NONE, eps_prune=0.0)
+    J2, K2 = oracle.jk(bas2, T @ D @ T.T, mode=oracle.SCREEN_NONE, eps_prune=0.0)
+    assert np.abs(J2 - T @ J @ T.T).max() < 1e-12
+    assert np.abs(K2 - T @ K @ T.T).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# J / K (Eq. fock_build) properties
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def small_case():
+    r = np.random.Generator(np.random.PCG64(77))
+    bas = molgen.random_shells(r, [0, 1, 2, 0, 3, 1], spread=1.5)
+    n = oracle.nbf(bas)
+    D = r.uniform(-1, 1, (n, n))
+    return bas, D + D.T
+
+
+def test_jk_symmetric_linear_psd(small_case, rng):
+    bas, D = small_case
+    J, K = oracle.jk(bas, D, mode=oracle.SCREEN_NONE, eps_prune=0.0)
+    assert np.abs(J - J.T).max() < 1e-13 and np.abs(K - K.T).max() < 1e-13
+    D2 = rng.uniform(-1, 1, D.shape)
+    D2 = D2 + D2.T
+    J2, K2 = oracle.jk(bas, D2, mode=oracle.SCREEN_NONE, eps_prune=0.0)
+    J3, K3 = oracle.jk(bas, D + 2 * D2, mode=oracle.SCREEN_NONE, eps_prune=0.0)
+    assert np.abs(J3 - (J + 2 * J2)).max() < 1e-12 and np.abs(K3 - (K + 2 * K2)).max() < 1e-12
+    # Coulomb and exchange energies of a symmetric D are non-negative
+    assert np.sum(D * J) > 0 and np.sum(D * K) > 0
+    assert np.sum(D2 * J2) > 0 and np.sum(D2 * K2) > 0
+
+
+def test_jk_symmetric_scatter_matches_all_quartets(small_case):
+    bas, D = small_case
+    for mode, tau, eps in [(oracle.SCREEN_NONE, 0.0, 0.0), (oracle.SCREEN_DENSITY, 1e-3, 1e-3)]:
+        J1, K1 = oracle.jk(bas, D, tau=tau, mode=mode, eps_prune=eps, symmetric=True)
+        J2, K2 = oracle.jk(bas, D, tau=tau, mode=mode, eps_prune=eps, symmetric=False)
+        assert np.abs(J1 - J2).max() < 1e-12 and np.abs(K1 - K2).max() < 1e-12
+
+
+def test_probe_density_recovers_eris(small_case):
+    """D = e_ls + e_sl gives J_mn = 2 (mn|ls) and K_mn = (ml|ns) + (ms|nl)."""
+    bas, _ = small_case
+    n = oracle.nbf(bas)
+    offs = np.concatenate([[0], np.cumsum([oracle.ncart(int(l)) for l in bas["l"]])])
+    a, b, c, d = 1, 2, 4, 5
+    e = oracle.shell_eri(bas, a, b, c, d)
+    lam, sig = offs[c] + 1, offs[d] + 2
+    D = np.zeros((n, n))
+    D[lam, sig] = D[sig, lam] = 1.0
+    J, K = oracle.jk(bas, D, mode=oracle.SCREEN_NONE, eps_prune=0.0)
+    blkJ = J[offs[a]:offs[a + 1], offs[b]:offs[b + 1]]
+    assert np.abs(blkJ - 2 * e[:, :, 1, 2]).max() < 1e-13
+    # K_mn = (m lam | n sig) + (m sig | n lam)
+    e2 = oracle.shell_eri(bas, a, c, b, d)
+    e3 = oracle.shell_eri(bas, a, d, b, c)
+    blkK = K[offs[a]:offs[a + 1], offs[b]:offs[b + 1]]
+    assert np.abs(blkK - (e2[:, 1, :, 2] + e3[:, 2, :, 1])).max() < 1e-13
+
+
+def test_blocks_match_full(small_case):
+    bas, D = small_case
+    J, K = oracle.jk(bas, D, tau=1e-4, mode=oracle.SCREEN_DENSITY, eps_prune=1e-3)
+    offs = np.concatenate([[0], np.cumsum([oracle.ncart(int(l)) for l in bas["l"]])])
+    pairs = [(0, 0), (2, 1), (4, 4), (1, 5), (5, 3)]
+    Jb, Kb = oracle.jk_blocks(bas, D, pairs, tau=1e-4, mode=oracle.SCREEN_DENSITY, eps_prune=1e-3)
+    for (a, b), jb, kb in zip(pairs, Jb, Kb):
+        assert np.abs(J[offs[a]:offs[a + 1], offs[b]:offs[b + 1]] - jb).max() < 1e-13
+        assert np.abs(K[offs[a]:offs[a + 1], offs[b]:offs[b + 1]] - kb).max() < 1e-13
+
+
+def test_screening_error_bounded():
+    """Each skipped contracted quartet moves a J or K element by at most
+    (number of its terms) x G_ab G_cd Dmax < 100 tau; the crude rigorous bound
+    below sums that over every quartet that can feed one element."""
+    r = np.random.Generator(np.random.PCG64(5))
+    bas = molgen.random_shells(r, [0, 1, 2, 0, 1, 2, 0, 1], spread=5.0)
+    n = oracle.nbf(bas)
+    D = r.uniform(-1, 1, (n, n))
+    D = D + D.T
+    tau = 1e-4
+    J0, K0 = oracle.jk(bas, D, mode=oracle.SCREEN_NONE, eps_prune=0.0)
+    J2, K2 = oracle.jk(bas, D, tau=tau, mode=oracle.SCREEN_DENSITY, eps_prune=0.0)
+    ns = len(bas["l"])
+    bound = 8 * ns * ns * 36 * tau
+    assert np.abs(J0 - J2).max() <= bound and np.abs(K0 - K2).max() <= bound
+    assert np.abs(J0 - J2).max() > 0 or np.abs(K0 - K2).max() > 0  # something was screened
+    cnt = oracle.count(bas, D, tau)
+    assert cnt["quartets_density"] < ns * (ns + 1) // 2 * (ns * (ns + 1) // 2 + 1) // 2
+
+
+def test_count_matches_brute_force():
+    p = molgen.problem(0)
+    G, _ = oracle.schwarz(p.basis)
+    ls = p.basis["l"]
+    ns = len(ls)
+    q = e = 0
+    for a in range(ns):
+        for b in range(a + 1):
+            for c in range(a + 1):
+                for d in range(c + 1):
+                    if (c, d) > (a, b):
+                        continue
+                    if G[a, b] * G[c, d] >= p.tau:
+                        q += 1
+                        e += np.prod([oracle.ncart(int(ls[s])) for s in (a, b, c, d)])
+    cnt = oracle.count(p.basis, p.D, p.tau)
+    assert cnt["quartets_schwarz"] == q and cnt["eris_schwarz"] == e
