@@ -21,8 +21,9 @@
  * Readings of the paper taken here (garbled or silent passages):
  *   - the auxiliary integral is [00|00]^(m) = U_P U_Q (2 theta / sqrt(pi)) F_m(T);
  *   - in vrr2 the PQ coefficient is W-Q = +zeta/(zeta+eta) (P-Q);
- *   - screening skips a quartet iff G_ab G_cd Dmax < tau with Dmax the largest
- *     |D| over the six shell blocks ab, ac, ad, bc, bd, cd (Sec. 3.2);
+ *   - screening skips a quartet iff G_ab G_cd < tau (pre-launch batch test)
+ *     or G_ab G_cd Dmax < tau with Dmax the largest |D| over the six shell
+ *     blocks ab, ac, ad, bc, bd, cd (in-kernel test), both Sec. 3.2;
  *   - a primitive pair is dropped iff G_[ab] * Gmax < tau * eps_p, Gmax the
  *     largest contracted G_ab (primitive-level pruning, Sec. 3.2).
  *
@@ -626,7 +627,9 @@ static int or_screened(const or_jk_setup *S, int a, int b, int c, int d) {
   dm = fmax(dm, Q[(size_t)a * ns + d]);
   dm = fmax(dm, Q[(size_t)b * ns + c]);
   dm = fmax(dm, Q[(size_t)b * ns + d]);
-  return g * dm < S->tau;
+  /* Sec. 3.2 applies both tests: batches whose Schwarz product is below tau
+   * are never launched, and inside the kernel G_ab G_cd Dmax < tau skips. */
+  return g < S->tau || g * dm < S->tau;
 }
 
 /*
