@@ -1,0 +1,293 @@
+"""Benchmark of the J/K build (one step = one fock_build_jk call, i.e. one SCF
+iteration's Coulomb + exchange build) on the C20H42 zigzag alkane workload
+(384 Cartesian functions, 6-31G(d)-shaped synthetic basis, FP64, Schwarz
+threshold 1e-10, distance-decaying synthetic density).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is ERIs/s: symmetry-unique contracted
+Cartesian ERIs in quartets passing the Schwarz test, divided by the device
+time of the build, summed over ranks (independent replicas, weak scaling).
+The reference arm times the CPU oracle (plain FP64 C with OpenMP) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "J+K build s/iteration and ERIs/s vs FP64/FP32 peak; mixed vs FP64 at 1e-7"
+UNIT = "ERI/s"
+# FP64 peak derived from the GB300 unit counts and clock: 152 SMs x 2 FP64
+# FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(p, st):
+    return {"workload": "C20H42 zigzag alkane, 6-31G(d)-shaped synthetic basis" if p.meta.get("config") == 1
+            else p.name, "nbf": int(p.nbf), "nshell": int(len(p.basis["l"])), "schwarz_thresh": p.tau,
+            "screening": "Schwarz + six-block density (Sec. 3.2)", "precision": "fp64",
+            "eris_per_step": int(st["eris_schwarz"]), "quartets_per_step": int(st["quartets_schwarz"]),
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def profile_traffic(kernel_src_hash: str):
+    """DRAM traffic per launch of the ERI kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "jk_c20h42_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_source_sha256") != kernel_src_hash:
+        return None
+    return d.get("dram_bytes_per_build")
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2407_21445_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_2407_21445_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def cpu_baseline(p, target_s=12.0):
+    """The oracle as it stands, on every host core, over a sample of outer shell
+    pairs (every stride-th) of the same workload."""
+    import oracle
+    t0 = time.perf_counter()
+    n0 = oracle.jk_sample(p.basis, p.D, p.tau, 64)
+    t1 = time.perf_counter() - t0
+    stride = max(1, int(round(64 * t1 / target_s)))
+    t0 = time.perf_counter()
+    n = oracle.jk_sample(p.basis, p.D, p.tau, stride)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"every {stride}th outer shell pair of the symmetric quartet loop "
+                      f"({n:.4g} Schwarz-passing ERIs, {dt:.1f} s incl. Schwarz setup)"}
+
+
+def run_reference(args, rank, world):
+    import molgen
+    import oracle
+    if rank != 0:
+        return
+    p = molgen.problem(args.config)
+    cnt = oracle.count(p.basis, p.D, p.tau)
+    t0 = time.perf_counter()
+    oracle.jk_sample(p.basis, p.D, p.tau, 64)
+    t1 = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)  # whole run within a few minutes
+    stride = max(1, int(round(64 * t1 / budget)))
+    for _ in range(args.warmup):
+        oracle.jk_sample(p.basis, p.D, p.tau, stride)
+    tot_n, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        tot_n += oracle.jk_sample(p.basis, p.D, p.tau, stride)
+        tot_t += time.perf_counter() - t0
+    value = tot_n / tot_t
+    st = {"eris_schwarz": cnt["eris_schwarz"], "quartets_schwarz": cnt["quartets_schwarz"]}
+    cfg = workload_config(p, st)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"every {stride}th outer shell pair per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    import molgen
+    import paper_2407_21445_gb300 as fk
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    p = molgen.problem(args.config)
+    builder = fk.JKBuilder(p.basis, p.tau)
+    st = builder.stats(p.D)
+    nk = fk.fock_kernels_per_build(builder.handle)
+    D = torch.tensor(p.D, device=dev, dtype=torch.float64)
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(max(3, args.warmup)):
+        builder.build(D, J, K)
+    torch.cuda.synchronize(dev)
+    st_code = fk.fock_stream_status()
+    if st_code != 0:
+        raise SystemExit(f"device status {fk.fock_status_string(st_code)}")
+
+    # ---- device-timed region ------------------------------------------------
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev.index) as clk:
+        for s, e in evs:
+            flush.zero_()
+            s.record(stream)
+            builder.build(D, J, K)
+            e.record(stream)
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in evs]
+    tot_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms = tot_ms / args.steps
+    value = world * st["eris_schwarz"] * args.steps / (tot_ms * 1e-3)
+
+    # ---- end-to-end: pinned host D in, J and K back to pinned host ----------
+    Dh = torch.tensor(p.D, dtype=torch.float64).pin_memory()
+    Jh = torch.empty_like(Dh).pin_memory()
+    Kh = torch.empty_like(Dh).pin_memory()
+    e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e_s.record(stream)
+    for _ in range(args.steps):
+        D.copy_(Dh, non_blocking=True)
+        builder.build(D, J, K)
+        Jh.copy_(J, non_blocking=True)
+        Kh.copy_(K, non_blocking=True)
+    e_e.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e_s.elapsed_time(e_e)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * st["eris_schwarz"] * args.steps / (e2e_ms * 1e-3)
+    assert np.isfinite(Jh.numpy()).all() and np.isfinite(Kh.numpy()).all()
+
+    if rank == 0:
+        achieved = st["fp64_flops_model"] / (ms * 1e-3) / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "s_per_iteration": ms * 1e-3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(p, st),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": profile_traffic(kernel_hash()),
+                         "peak_note": "FP64 pipe, derived 152 SMs x 2 FMA/clk x 2.07 GHz; achieved = modelled "
+                                      "FP64 flops of evaluated quartets / device time of the whole build"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(D.numel() * 8),
+                    "d2h_bytes_per_step": int(2 * D.numel() * 8)},
+            "gpu_launches": int(nk * args.steps),
+            "clocks": clk.summary(),
+            "work": {k: st[k] for k in ("quartets_evaluated", "eris_evaluated", "prim_quartets",
+                                        "fp64_flops_model", "prim_pairs", "pairs")},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(p)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

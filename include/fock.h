@@ -1,0 +1,209 @@
+/*
+ * fock.h -- C ABI of the GB300 Coulomb/exchange (J/K) builder.
+ *
+ * The library builds, for a contracted Cartesian Gaussian basis up to f
+ * functions and a symmetric density matrix D,
+ *
+ *     J_mn = sum_ls (mn|ls) D_ls,     K_mn = sum_ls (ml|ns) D_ls
+ *
+ * (arXiv:2407.21445, Sec. 2.2, Eq. fock_build), from two-electron repulsion
+ * integrals (Sec. 2.1) evaluated with the McMurchie-Davidson Hermite scheme
+ * (Sec. 4.1, Eqs. MD def, EabP def1-3) and a tabulated Boys function
+ * (Eq. boys-fn-def), screened with the Cauchy-Schwarz bound (Eqs.
+ * cauchy-schwarz 1, 2) weighted by the density (Sec. 3.2).
+ *
+ * Conventions shared by every entry point
+ *   - Geometry in bohr, exponents in bohr^-2.
+ *   - Cartesian functions of a shell are ordered x^l, x^(l-1)y, x^(l-1)z, ...,
+ *     z^l (x exponent descending, then y descending); each Cartesian function
+ *     is normalised to unit self-overlap.
+ *   - D, J, K are N x N row-major float64 matrices in device memory, owned by
+ *     the caller; J and K are overwritten with full symmetric matrices.
+ *   - Work is asynchronous on the given CUDA stream; argument errors are
+ *     returned synchronously, device-side errors (non-finite density, a work
+ *     queue wait that timed out) are recorded in a device status word read by
+ *     fock_stream_status().
+ *   - No entry point traps, asserts or aborts on the device.
+ */
+#ifndef FOCK_H
+#define FOCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define FOCK_API __attribute__((visibility("default")))
+#else
+#define FOCK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FOCK_OK = 0,
+  FOCK_ERR_INVALID_ARG = 1,    /* null pointer, bad size, bad threshold      */
+  FOCK_ERR_UNSUPPORTED_L = 2,  /* angular momentum > 3 or contraction > 8    */
+  FOCK_ERR_NONFINITE = 3,      /* NaN/Inf found in the density (device)      */
+  FOCK_ERR_OOM = 4,            /* device or host allocation failed           */
+  FOCK_ERR_CUDA = 5,           /* a CUDA runtime call failed                 */
+  FOCK_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up         */
+  FOCK_ERR_NOT_CONVERGED = 7   /* iterative driver did not converge          */
+} fock_status;
+
+enum { FOCK_FP64 = 0, FOCK_MIXED = 1 };
+
+/* Basis description: host pointers, caller-owned, read only during
+ * fock_shellpairs_build.  Shell s has angular momentum l[s] (0..3), nprim[s]
+ * (1..8) primitives whose exponents and raw contraction coefficients (for
+ * primitive-normalised Gaussians, Sec. 2.1 Eq. prim) are exps/coefs[prim_off[s]
+ * .. prim_off[s]+nprim[s]-1]; centre[3*s..3*s+2] in bohr; atom[s] is the
+ * index of the atom carrying the shell (may be NULL). */
+typedef struct {
+  int32_t nshell;
+  const double *center;
+  const int32_t *l;
+  const int32_t *nprim;
+  const int32_t *prim_off;
+  const double *exps;
+  const double *coefs;
+  const int32_t *atom;
+} fock_basis_desc;
+
+/* Options; pass NULL for the defaults shown. */
+typedef struct {
+  int32_t precision;    /* FOCK_FP64 (default) or FOCK_MIXED                     */
+  double fp32_cutoff;   /* mixed path: quartets with G_ab G_cd Dmax below this
+                           bound are evaluated in FP32 (default 1e-5)           */
+  double prune_eps;     /* primitive pair [ab] dropped when G_[ab] Gmax <
+                           tau * prune_eps (default 1e-3; 0 disables)           */
+  int32_t group_override; /* 0 = autotuned per class pair; 1..32 = lanes per
+                             quartet forced for every class pair (testing)     */
+  int32_t reserved[7];
+} fock_opts;
+
+typedef struct fock_shellpairs fock_shellpairs; /* opaque, library-owned */
+
+/*
+ * Build the shell-pair data for one geometry (Sec. 3.2 batching and
+ * primitive screening, Sec. 4.2 sorted pair lists): normalisation,
+ * primitive pairs (zeta, P, U_P; Sec. 2.1 Eq. zeta), Hermite expansion
+ * coefficients E^{ab}_p (Sec. 4.1 Eqs. EabP def1-3), Schwarz factors G_ab and
+ * G_[ab] from diagonal integrals computed on the GPU (Eqs. cauchy-schwarz 1,
+ * 2), primitive-pair pruning, and the quartet work lists of pairs binned by
+ * angular-momentum class and contraction degree whose Schwarz product is at
+ * least schwarz_thresh.
+ *   desc, opts: host, read during the call.   schwarz_thresh > 0.
+ *   stream: the CUDA stream the build's kernels run on; the call
+ *   synchronises that stream before returning.
+ *   *out receives a handle owned by the library (free with
+ *   fock_shellpairs_free); it is immutable afterwards and may be shared by
+ *   calls on several streams.
+ * Errors: FOCK_ERR_INVALID_ARG (null pointers, nshell < 1, bad exponents or
+ * offsets, threshold <= 0), FOCK_ERR_UNSUPPORTED_L (l > 3, nprim > 8),
+ * FOCK_ERR_OOM, FOCK_ERR_CUDA.  On error *out is set to NULL.
+ */
+FOCK_API fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *opts,
+                                  double schwarz_thresh, cudaStream_t stream,
+                                  fock_shellpairs **out);
+
+/* Release a handle (NULL is accepted).  The caller must ensure no work using
+ * it is still in flight. */
+FOCK_API fock_status fock_shellpairs_free(fock_shellpairs *sp);
+
+/* Number of Cartesian basis functions N of the handle (-1 for NULL). */
+FOCK_API int32_t fock_nbasis(const fock_shellpairs *sp);
+
+/*
+ * J and K for one density (Sec. 2.2 Eq. fock_build), one SCF iteration of the
+ * direct method (Sec. 2.2): every symmetry-unique contracted shell quartet
+ * (Sec. 2.3, 8-fold symmetry) whose density-weighted Schwarz bound
+ * G_ab G_cd max(|D_ab|,|D_ac|,|D_ad|,|D_bc|,|D_bd|,|D_cd|) is not below
+ * schwarz_thresh (Sec. 3.2) is evaluated and digested into J and K.
+ *   D: device, N x N row-major float64, symmetric (read).
+ *   J, K: device, N x N row-major float64 (overwritten).
+ *   schwarz_thresh >= the value the handle was built with.
+ *   stream: all work is enqueued on it; no host synchronisation.
+ * Per-call scratch (shell-block density maxima, work counters) is taken from
+ * the stream-ordered allocator (cudaMallocAsync) and released on the stream.
+ * Errors (synchronous): FOCK_ERR_INVALID_ARG (null pointers, threshold below
+ * the build threshold), FOCK_ERR_OOM, FOCK_ERR_CUDA.  A NaN/Inf in D sets
+ * FOCK_ERR_NONFINITE in the status word (fock_stream_status).
+ */
+FOCK_API fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double schwarz_thresh,
+                          double *J, double *K, cudaStream_t stream);
+
+/*
+ * J and K for nmol independent molecules in one pass: bases[i], D[i], J[i],
+ * K[i] as in fock_build_jk (all device pointers; the pointer arrays themselves
+ * are host memory read during the call).
+ */
+FOCK_API fock_status fock_build_jk_batched(const fock_shellpairs *const *bases, int32_t nmol,
+                                  const double *const *D, double schwarz_thresh,
+                                  double *const *J, double *const *K, cudaStream_t stream);
+
+/*
+ * Work statistics of the handle for the given density and threshold,
+ * computed on the host from the handle's pair data and a host copy of the
+ * shell-block density maxima:
+ *   out[0] symmetry-unique contracted quartets passing Schwarz (G_ab G_cd >= tau)
+ *   out[1] Cartesian ERIs in those quartets (throughput unit)
+ *   out[2] quartets also passing the density-weighted test (evaluated)
+ *   out[3] Cartesian ERIs in evaluated quartets
+ *   out[4] primitive quartets evaluated
+ *   out[5] modelled FP64 floating-point operations of the evaluated work
+ *          (per-class Hermite-scheme counts: Boys, R recursion, ket and bra
+ *          Hermite transforms, digestion)
+ *   out[6] primitive pairs kept after pruning
+ *   out[7] contracted pairs kept
+ * D: host, N x N row-major float64.  Synchronous.
+ */
+FOCK_API fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host,
+                            double schwarz_thresh, double out[8]);
+
+/* Number of kernels one fock_build_jk call on this handle launches (density
+ * preparation, one persistent ERI/digestion kernel per work tier, the final
+ * symmetrisation); -1 for NULL.  Host only. */
+FOCK_API int32_t fock_kernels_per_build(const fock_shellpairs *sp);
+
+/* Synchronise the stream, return and clear the device status word
+ * (FOCK_OK if no device-side error was recorded). */
+FOCK_API fock_status fock_stream_status(cudaStream_t stream);
+
+/* Human-readable name of a status code (static storage). */
+FOCK_API const char *fock_status_string(fock_status st);
+
+/*
+ * Host-side inspection of the handle's precomputed tables, for tests (no
+ * device work; safe without a GPU once a handle exists):
+ * Boys table parameters: out[0] grid step h, out[1] number of grid points,
+ * out[2] number of orders stored, out[3] T beyond which the asymptotic form
+ * is used.
+ */
+FOCK_API fock_status fock_boys_table_info(double out[4]);
+
+/*
+ * Host evaluation of the library's own tabulated Boys function (same table
+ * and Taylor rule the kernels use), F_m(T) for m = 0..mmax into F.
+ * For tests of the table against independent evaluations.
+ */
+FOCK_API fock_status fock_boys_host(int32_t mmax, double T, double *F);
+
+/*
+ * Hermite expansion coefficients E^{ab}_{tuv} (Sec. 4.1, Eqs. EabP def1-3)
+ * of one primitive pair, as the kernels store them: for every Cartesian pair
+ * (a component major, b component minor) the box t<=ax+bx, u<=ay+by,
+ * v<=az+bz in t-major order, WITHOUT the Cartesian normalisation factors.
+ * out must hold fock_hermite_count(la, lb) doubles.  alpha/A on shell a,
+ * beta/B on shell b.  Host only.
+ */
+FOCK_API int32_t fock_hermite_count(int32_t la, int32_t lb);
+FOCK_API fock_status fock_hermite_e(int32_t la, int32_t lb, double alpha, const double *A, double beta,
+                           const double *B, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FOCK_H */

@@ -54,6 +54,7 @@ def lib():
             _lib.oracle_jk.argtypes = basis + [p, d, i, d, i, i, p, p]
             _lib.oracle_jk_blocks.argtypes = basis + [p, d, i, d, i, p, p, i, p, p]
             _lib.oracle_count.argtypes = basis + [p, d, p]
+            _lib.oracle_jk_sample.argtypes = basis + [p, d, i, d, i, i, p, p, p]
     return _lib
 
 
@@ -154,6 +155,29 @@ def jk(basis: dict, D: np.ndarray, tau: float = 0.0, mode: int = SCREEN_DENSITY,
     if rc:
         raise ValueError("bad basis")
     return J, K
+
+
+def jk_sample(basis: dict, D: np.ndarray, tau: float, stride: int, nthreads: int = 0,
+              mode: int = SCREEN_DENSITY, eps_prune: float = EPS_PRUNE):
+    """The symmetric J/K loop over every stride-th outer shell pair only (a
+    bounded sample of the full build, used to time the oracle); returns the
+    number of Schwarz-passing Cartesian ERIs in the sampled quartets."""
+    args, keep = _basis_args(basis)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    n = nbf(basis)
+    J = np.zeros((n, n))
+    K = np.zeros((n, n))
+    neri = np.zeros(1)
+    rc = lib().oracle_jk_sample(*args, _ptr(D), float(tau), int(mode), float(eps_prune), int(nthreads),
+                                int(stride), _ptr(J), _ptr(K), _ptr(neri))
+    if rc:
+        raise ValueError("bad basis")
+    return float(neri[0])
+
+
+def threads() -> int:
+    """Threads the oracle's OpenMP loops use by default."""
+    return os.cpu_count() or 1
 
 
 def jk_blocks(basis: dict, D: np.ndarray, pairs, tau: float, mode: int = SCREEN_DENSITY,

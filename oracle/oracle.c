@@ -639,10 +639,10 @@ static int or_screened(const or_jk_setup *S, int a, int b, int c, int d) {
  * otherwise over all ordered quartets (N^4 reference used to validate the
  * scatter on small cases).  Returns 0 on success.
  */
-int oracle_jk(int nshell, const double *center, const int32_t *l, const int32_t *nprim,
-              const int32_t *prim_off, const double *exps, const double *coefs, const double *Dm,
-              double tau, int mode, double eps_p, int symmetric, int nthreads, double *J,
-              double *K) {
+static int or_jk_impl(int nshell, const double *center, const int32_t *l, const int32_t *nprim,
+                      const int32_t *prim_off, const double *exps, const double *coefs,
+                      const double *Dm, double tau, int mode, double eps_p, int symmetric,
+                      int nthreads, int stride, double *J, double *K, double *neri) {
   or_basis B = {nshell, center, l, nprim, prim_off, exps, coefs};
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -669,6 +669,7 @@ int oracle_jk(int nshell, const double *center, const int32_t *l, const int32_t 
         ++k;
       }
   }
+  double cnt = 0.0;
 #pragma omp parallel
   {
     int tid = 0;
@@ -679,15 +680,17 @@ int oracle_jk(int nshell, const double *center, const int32_t *l, const int32_t 
     or_work w;
     or_work_alloc(&w);
     double *eri = (double *)malloc(sizeof(double) * 10000);
-#pragma omp for schedule(dynamic, 1)
+#pragma omp for schedule(dynamic, 1) reduction(+ : cnt)
     for (int p1 = 0; p1 < npair; ++p1) {
+      if (p1 % stride) continue;
       int a = pa[p1], b = pb[p1];
       for (int p2 = 0; p2 < (symmetric ? p1 + 1 : npair); ++p2) {
         int c = pa[p2], d = pb[p2];
-        if (or_screened(&S, a, b, c, d)) continue;
-        or_shell_quartet(&S.X, &w, a, b, c, d, -1, -1, eri);
         int na = off[a + 1] - off[a], nb = off[b + 1] - off[b], nc = off[c + 1] - off[c],
             nd = off[d + 1] - off[d];
+        if (S.G[(size_t)a * ns + b] * S.G[(size_t)c * ns + d] >= tau) cnt += (double)na * nb * nc * nd;
+        if (or_screened(&S, a, b, c, d)) continue;
+        or_shell_quartet(&S.X, &w, a, b, c, d, -1, -1, eri);
         for (int i = 0; i < na; ++i)
           for (int j = 0; j < nb; ++j)
             for (int k = 0; k < nc; ++k)
@@ -742,7 +745,29 @@ int oracle_jk(int nshell, const double *center, const int32_t *l, const int32_t 
   free(pa);
   free(pb);
   or_setup_free(&S);
+  if (neri) *neri = cnt;
   return 0;
+}
+
+int oracle_jk(int nshell, const double *center, const int32_t *l, const int32_t *nprim,
+              const int32_t *prim_off, const double *exps, const double *coefs, const double *Dm,
+              double tau, int mode, double eps_p, int symmetric, int nthreads, double *J,
+              double *K) {
+  return or_jk_impl(nshell, center, l, nprim, prim_off, exps, coefs, Dm, tau, mode, eps_p, symmetric,
+                    nthreads, 1, J, K, NULL);
+}
+
+/* The symmetric J/K loop restricted to outer pairs p1 with p1 % stride == 0
+ * (a bounded sample of the full build, for CPU timing); *neri receives the
+ * number of Cartesian ERIs in the sampled quartets that pass the Schwarz
+ * test, the same unit the GPU throughput is quoted in. */
+int oracle_jk_sample(int nshell, const double *center, const int32_t *l, const int32_t *nprim,
+                     const int32_t *prim_off, const double *exps, const double *coefs,
+                     const double *Dm, double tau, int mode, double eps_p, int nthreads, int stride,
+                     double *J, double *K, double *neri) {
+  if (stride < 1) return 1;
+  return or_jk_impl(nshell, center, l, nprim, prim_off, exps, coefs, Dm, tau, mode, eps_p, 1,
+                    nthreads, stride, J, K, neri);
 }
 
 /*

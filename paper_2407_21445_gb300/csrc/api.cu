@@ -1,0 +1,638 @@
+// C-ABI entry points of the J/K builder (declared in include/fock.h) and the
+// shell-pair handle construction.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "fock_impl.h"
+
+using namespace fk;
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383;
+
+struct Staging {  // host arrays mirroring DevPairs
+  std::vector<double> sxyz;
+  std::vector<int> sbf, sl;
+  std::vector<int2> ab;
+  std::vector<double> G;
+  std::vector<int2> prim;
+  std::vector<int> cls;
+  std::vector<PZ> pz;
+  std::vector<double> U;
+  std::vector<int> eoff;
+  std::vector<double> E;
+};
+
+// Device copy of a Staging set plus units: one allocation, 256-byte aligned
+// sub-buffers.  Returns the base pointer; fills dp and unit pointers.
+struct Packer {
+  size_t off = 0;
+  std::vector<std::pair<size_t, std::pair<const void *, size_t>>> parts;
+  size_t add(const void *src, size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    size_t at = off;
+    parts.push_back({at, {src, bytes}});
+    off += bytes;
+    return at;
+  }
+};
+
+fock_status to_status(cudaError_t e) {
+  if (e == cudaSuccess) return FOCK_OK;
+  if (e == cudaErrorMemoryAllocation) return FOCK_ERR_OOM;
+  return FOCK_ERR_CUDA;
+}
+
+// Scratch (doubles) one group needs for a quartet of bra class cb, ket class ck.
+int scratch_doubles(int la, int lb, int lc, int ld) {
+  const int nab = ncart(la) * ncart(lb), ncd = ncart(lc) * ncart(ld);
+  const int Lab = la + lb, L = la + lb + lc + ld;
+  return nab * ncd + nherm(Lab) * ncd + 2 * nherm(L) + L + 2;
+}
+
+void class_l(int c, int &la, int &lb) {
+  la = 0;
+  while ((la + 1) * (la + 2) / 2 <= c) ++la;
+  lb = c - la * (la + 1) / 2;
+}
+
+// FP64 operation model of one primitive quartet (Boys Taylor, seeds, R
+// recursion, ket transform) and per bra primitive (bra transform).
+double flops_prim(int Lab, int L, int ck) {
+  const ClassTables &ct = class_tables();
+  double f = 30.0;                  // alpha, T, prefactor
+  f += (L + 1) * (2.0 * 7 + 1.0);   // Taylor Horner + seed scaling
+  for (int n = L - 1; n >= 0; --n)  // Hermite recursion
+    for (int e = 1; e < nherm(L - n); ++e) {
+      const int t = ct.hvec[e][0], u = ct.hvec[e][1], w = ct.hvec[e][2];
+      const int c = t > 0 ? t : (u > 0 ? u : w);
+      f += c > 1 ? 3.0 : 1.0;
+    }
+  f += 2.0 * nherm(Lab) * ct.nE[ck];
+  return f;
+}
+
+double flops_bra(int cb, int ncd) { return 2.0 * class_tables().nE[cb] * ncd; }
+
+// flops_prim / flops_bra per (bra class, ket class), cached
+struct FlopTable {
+  double prim[NCLASS][NCLASS], bra[NCLASS][NCLASS];
+  FlopTable() {
+    for (int cb = 0; cb < NCLASS; ++cb)
+      for (int ck = 0; ck < NCLASS; ++ck) {
+        int la, lb, lc, ld;
+        class_l(cb, la, lb);
+        class_l(ck, lc, ld);
+        prim[cb][ck] = flops_prim(la + lb, la + lb + lc + ld, ck);
+        bra[cb][ck] = flops_bra(cb, ncart(lc) * ncart(ld));
+      }
+  }
+};
+const FlopTable &flop_table() {
+  static FlopTable t;
+  return t;
+}
+
+int bucket_of(int nprim) {
+  int b = 0;
+  while ((1 << b) < nprim) ++b;
+  return b;  // 1 -> 0, 2 -> 1, 3..4 -> 2, 5..8 -> 3, ...
+}
+
+fock_status validate(const fock_basis_desc *d) {
+  if (!d || d->nshell < 1 || !d->center || !d->l || !d->nprim || !d->prim_off || !d->exps || !d->coefs)
+    return FOCK_ERR_INVALID_ARG;
+  for (int s = 0; s < d->nshell; ++s) {
+    if (d->l[s] < 0 || d->l[s] > LMAX) return FOCK_ERR_UNSUPPORTED_L;
+    if (d->nprim[s] < 1 || d->nprim[s] > MAXPRIM) return FOCK_ERR_UNSUPPORTED_L;
+    if (d->prim_off[s] < 0) return FOCK_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k)
+      if (!isfinite(d->center[3 * s + k])) return FOCK_ERR_INVALID_ARG;
+    for (int i = 0; i < d->nprim[s]; ++i) {
+      const double a = d->exps[d->prim_off[s] + i], c = d->coefs[d->prim_off[s] + i];
+      if (!(a > 0.0) || !isfinite(a) || !isfinite(c)) return FOCK_ERR_INVALID_ARG;
+    }
+  }
+  return FOCK_OK;
+}
+
+// Normalised contraction coefficients: raw coefficient x primitive factor
+// (2a/pi)^{3/4} (4a)^{l/2} x contracted factor making every Cartesian
+// function of unit norm (the component factor 1/sqrt(prod (2k-1)!!) is folded
+// into the Hermite coefficients).
+void norm_coefs(const fock_basis_desc *d, int s, double *out) {
+  const int l = d->l[s], K = d->nprim[s], o = d->prim_off[s];
+  double S = 0.0;
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j) {
+      const double ai = d->exps[o + i], aj = d->exps[o + j];
+      S += d->coefs[o + i] * d->coefs[o + j] * pow(2.0 * sqrt(ai * aj) / (ai + aj), l + 1.5);
+    }
+  const double nc = 1.0 / sqrt(S);
+  for (int i = 0; i < K; ++i) {
+    const double a = d->exps[o + i];
+    out[i] = nc * d->coefs[o + i] * pow(2.0 * a / kPi, 0.75) * pow(4.0 * a, 0.5 * l);
+  }
+}
+
+fock_status upload(const Staging &st, const std::vector<Unit> &units, void **base, DevPairs &dp, Unit **d_units,
+                   size_t *bytes, cudaStream_t stream) {
+  Packer pk;
+  const size_t o_sxyz = pk.add(st.sxyz.data(), st.sxyz.size() * sizeof(double));
+  const size_t o_sbf = pk.add(st.sbf.data(), st.sbf.size() * sizeof(int));
+  const size_t o_sl = pk.add(st.sl.data(), st.sl.size() * sizeof(int));
+  const size_t o_ab = pk.add(st.ab.data(), st.ab.size() * sizeof(int2));
+  const size_t o_G = pk.add(st.G.data(), st.G.size() * sizeof(double));
+  const size_t o_prim = pk.add(st.prim.data(), st.prim.size() * sizeof(int2));
+  const size_t o_cls = pk.add(st.cls.data(), st.cls.size() * sizeof(int));
+  const size_t o_pz = pk.add(st.pz.data(), st.pz.size() * sizeof(PZ));
+  const size_t o_U = pk.add(st.U.data(), st.U.size() * sizeof(double));
+  const size_t o_eoff = pk.add(st.eoff.data(), st.eoff.size() * sizeof(int));
+  const size_t o_E = pk.add(st.E.data(), st.E.size() * sizeof(double));
+  const size_t o_units = pk.add(units.data(), units.size() * sizeof(Unit));
+  const size_t total = (pk.off + 255) & ~(size_t)255;
+  char *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, total > 0 ? total : 256);
+  if (e != cudaSuccess) return to_status(e);
+  for (auto &p : pk.parts) {
+    if (p.second.second == 0) continue;
+    e = cudaMemcpyAsync(d + p.first, p.second.first, p.second.second, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return to_status(e);
+    }
+  }
+  dp.sxyz = (const double *)(d + o_sxyz);
+  dp.sbf = (const int *)(d + o_sbf);
+  dp.sl = (const int *)(d + o_sl);
+  dp.ab = (const int2 *)(d + o_ab);
+  dp.G = (const double *)(d + o_G);
+  dp.prim = (const int2 *)(d + o_prim);
+  dp.cls = (const int *)(d + o_cls);
+  dp.pz = (const PZ *)(d + o_pz);
+  dp.U = (const double *)(d + o_U);
+  dp.eoff = (const int *)(d + o_eoff);
+  dp.E = (const double *)(d + o_E);
+  dp.npair = (int)st.ab.size();
+  if (d_units) *d_units = (Unit *)(d + o_units);
+  *base = d;
+  if (bytes) *bytes = total;
+  return FOCK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fock_status_string(fock_status st) {
+  switch (st) {
+    case FOCK_OK: return "FOCK_OK";
+    case FOCK_ERR_INVALID_ARG: return "FOCK_ERR_INVALID_ARG";
+    case FOCK_ERR_UNSUPPORTED_L: return "FOCK_ERR_UNSUPPORTED_L";
+    case FOCK_ERR_NONFINITE: return "FOCK_ERR_NONFINITE";
+    case FOCK_ERR_OOM: return "FOCK_ERR_OOM";
+    case FOCK_ERR_CUDA: return "FOCK_ERR_CUDA";
+    case FOCK_ERR_TIMEOUT: return "FOCK_ERR_TIMEOUT";
+    case FOCK_ERR_NOT_CONVERGED: return "FOCK_ERR_NOT_CONVERGED";
+  }
+  return "FOCK_ERR_UNKNOWN";
+}
+
+fock_status fock_boys_table_info(double out[4]) {
+  if (!out) return FOCK_ERR_INVALID_ARG;
+  out[0] = BOYS_H;
+  out[1] = BOYS_NGRID;
+  out[2] = BOYS_NORD;
+  out[3] = BOYS_TMAX;
+  return FOCK_OK;
+}
+
+fock_status fock_boys_host(int32_t mmax, double T, double *F) {
+  if (!F || mmax < 0 || mmax > LTOT || !(T >= 0.0) || !isfinite(T)) return FOCK_ERR_INVALID_ARG;
+  boys_eval_host(mmax, T, F);
+  return FOCK_OK;
+}
+
+int32_t fock_hermite_count(int32_t la, int32_t lb) {
+  if (la < 0 || lb < 0 || la > LMAX || lb > LMAX) return -1;
+  return hermite_count(la, lb);
+}
+
+fock_status fock_hermite_e(int32_t la, int32_t lb, double alpha, const double *A, double beta, const double *B,
+                           double *out) {
+  if (la < 0 || lb < 0 || la > LMAX || lb > LMAX || !A || !B || !out || !(alpha > 0) || !(beta > 0))
+    return FOCK_ERR_INVALID_ARG;
+  hermite_pair(la, lb, alpha, A, beta, B, false, out);
+  return FOCK_OK;
+}
+
+int32_t fock_nbasis(const fock_shellpairs *sp) { return sp ? sp->nbf : -1; }
+
+int32_t fock_kernels_per_build(const fock_shellpairs *sp) {
+  if (!sp) return -1;
+  int n = 2;  // density preparation + symmetrisation
+  for (const Tier &t : sp->tiers) n += t.nunits > 0 ? 1 : 0;
+  return n;
+}
+
+fock_status fock_shellpairs_free(fock_shellpairs *sp) {
+  if (!sp) return FOCK_OK;
+  if (sp->d_block) cudaFree(sp->d_block);
+  delete sp;
+  return FOCK_OK;
+}
+
+fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *opts, double schwarz_thresh,
+                                  cudaStream_t stream, fock_shellpairs **out) {
+  if (!out) return FOCK_ERR_INVALID_ARG;
+  *out = nullptr;
+  fock_status vs = validate(desc);
+  if (vs != FOCK_OK) return vs;
+  if (!(schwarz_thresh > 0.0) || !isfinite(schwarz_thresh)) return FOCK_ERR_INVALID_ARG;
+  fock_opts o{};
+  o.precision = FOCK_FP64;
+  o.fp32_cutoff = 1e-5;
+  o.prune_eps = 1e-3;
+  o.group_override = 0;
+  if (opts) o = *opts;
+  if (o.precision != FOCK_FP64 && o.precision != FOCK_MIXED) return FOCK_ERR_INVALID_ARG;
+  if (!(o.prune_eps >= 0.0) || o.group_override < 0 || o.group_override > 32 ||
+      (o.group_override & (o.group_override - 1)) != 0)
+    return FOCK_ERR_INVALID_ARG;
+
+  cudaError_t ce = upload_tables(stream);
+  if (ce != cudaSuccess) return to_status(ce);
+  const ClassTables &ct = class_tables();
+
+  fock_shellpairs *sp = new (std::nothrow) fock_shellpairs();
+  if (!sp) return FOCK_ERR_OOM;
+  cudaGetDevice(&sp->device);
+  sp->opts = o;
+  sp->tau_build = schwarz_thresh;
+  sp->prune_eps = o.prune_eps;
+  const int ns = desc->nshell;
+  sp->nshell = ns;
+
+  // ---- shells --------------------------------------------------------------
+  Staging st;
+  st.sxyz.assign(desc->center, desc->center + 3 * ns);
+  st.sl.assign(desc->l, desc->l + ns);
+  st.sbf.resize(ns);
+  int nbf = 0;
+  for (int s = 0; s < ns; ++s) {
+    st.sbf[s] = nbf;
+    nbf += ncart(desc->l[s]);
+  }
+  sp->nbf = nbf;
+  std::vector<std::vector<double>> cn(ns);
+  for (int s = 0; s < ns; ++s) {
+    cn[s].resize(desc->nprim[s]);
+    norm_coefs(desc, s, cn[s].data());
+  }
+
+  // ---- all canonical pairs with all primitive pairs -------------------------
+  Staging all = st;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b) {
+      const int la = desc->l[a], lb = desc->l[b];
+      if (!(la > lb || (la == lb && a >= b))) continue;
+      const double *A = desc->center + 3 * a, *B = desc->center + 3 * b;
+      const double AB2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
+      const int Ka = desc->nprim[a], Kb = desc->nprim[b];
+      const int first = (int)all.pz.size();
+      for (int i = 0; i < Ka; ++i)
+        for (int j = 0; j < Kb; ++j) {
+          const double al = desc->exps[desc->prim_off[a] + i], be = desc->exps[desc->prim_off[b] + j];
+          const double p = al + be;
+          const PZ pz{(al * A[0] + be * B[0]) / p, (al * A[1] + be * B[1]) / p, (al * A[2] + be * B[2]) / p, p};
+          all.pz.push_back(pz);
+          all.U.push_back(cn[a][i] * cn[b][j] * pow(kPi / p, 1.5) * exp(-al * be / p * AB2));
+          all.eoff.push_back((int)all.E.size());
+          const size_t e0 = all.E.size();
+          all.E.resize(e0 + ct.nE[pair_class(la, lb)]);
+          hermite_pair(la, lb, al, A, be, B, true, all.E.data() + e0);
+        }
+      all.ab.push_back(make_int2(a, b));
+      all.prim.push_back(make_int2(first, Ka * Kb));
+      all.cls.push_back(pair_class(la, lb));
+      all.G.push_back(0.0);
+    }
+  const int npair_all = (int)all.ab.size();
+  const int nprim_all = (int)all.pz.size();
+
+  // ---- Schwarz factors on the GPU ------------------------------------------
+  std::vector<double> Gpair(npair_all), Gprim(nprim_all);
+  {
+    void *base = nullptr;
+    DevPairs dp{};
+    std::vector<Unit> none;
+    fock_status s = upload(all, none, &base, dp, nullptr, nullptr, stream);
+    if (s != FOCK_OK) {
+      delete sp;
+      return s;
+    }
+    dp.nshell = ns;
+    dp.nbf = nbf;
+    double *dG = nullptr;
+    ce = cudaMalloc(&dG, sizeof(double) * (npair_all + nprim_all + 1));
+    if (ce == cudaSuccess) ce = launch_schwarz(dp, dG, dG + npair_all, stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(Gpair.data(), dG, sizeof(double) * npair_all, cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(Gprim.data(), dG + npair_all, sizeof(double) * nprim_all, cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    if (dG) cudaFree(dG);
+    cudaFree(base);
+    if (ce != cudaSuccess) {
+      delete sp;
+      return to_status(ce);
+    }
+  }
+
+  // ---- pruning (Sec. 3.2 primitive screening) -------------------------------
+  double gmax = 0.0;
+  for (double g : Gpair) gmax = std::max(gmax, g);
+  const double tau = schwarz_thresh;
+  struct PairRec {
+    int idx, cls, nkeep, bucket;
+    double G;
+  };
+  std::vector<PairRec> keep;
+  std::vector<std::vector<int>> kept_prims(npair_all);
+  for (int P = 0; P < npair_all; ++P) {
+    if (Gpair[P] * gmax < tau) continue;
+    const int2 pr = all.prim[P];
+    for (int i = pr.x; i < pr.x + pr.y; ++i)
+      if (!(o.prune_eps > 0.0 && Gprim[i] * gmax < tau * o.prune_eps)) kept_prims[P].push_back(i);
+    if (kept_prims[P].empty()) continue;
+    const int nk = (int)kept_prims[P].size();
+    keep.push_back({P, all.cls[P], nk, bucket_of(nk), Gpair[P]});
+  }
+  std::stable_sort(keep.begin(), keep.end(), [](const PairRec &x, const PairRec &y) {
+    if (x.cls != y.cls) return x.cls < y.cls;
+    if (x.bucket != y.bucket) return x.bucket < y.bucket;
+    return x.G > y.G;
+  });
+  const int npair = (int)keep.size();
+  for (const PairRec &r : keep) {
+    const int P = r.idx;
+    st.ab.push_back(all.ab[P]);
+    st.G.push_back(Gpair[P]);
+    st.cls.push_back(all.cls[P]);
+    st.prim.push_back(make_int2((int)st.pz.size(), r.nkeep));
+    for (int i : kept_prims[P]) {
+      st.pz.push_back(all.pz[i]);
+      st.U.push_back(all.U[i]);
+      st.eoff.push_back((int)st.E.size());
+      const int n = ct.nE[all.cls[P]];
+      st.E.insert(st.E.end(), all.E.begin() + all.eoff[i], all.E.begin() + all.eoff[i] + n);
+    }
+  }
+
+  // ---- bins and work units --------------------------------------------------
+  struct Bin {
+    int begin, end, cls, bucket;
+  };
+  std::vector<Bin> bins;
+  for (int i = 0; i < npair; ++i) {
+    if (bins.empty() || bins.back().cls != keep[i].cls || bins.back().bucket != keep[i].bucket)
+      bins.push_back({i, i, keep[i].cls, keep[i].bucket});
+    bins.back().end = i + 1;
+  }
+  struct Task {
+    int bra, ket;  // bin indices
+    bool same;
+    double cost;   // per quartet estimate
+    int G, scratch;
+  };
+  std::vector<Task> tasks;
+  for (int x = 0; x < (int)bins.size(); ++x)
+    for (int y = x; y < (int)bins.size(); ++y) {
+      const Bin &X = bins[x], &Y = bins[y];
+      int lxa, lxb, lya, lyb;
+      class_l(X.cls, lxa, lxb);
+      class_l(Y.cls, lya, lyb);
+      const double px = 1 << X.bucket, py = 1 << Y.bucket;
+      const int Lx = lxa + lxb, Ly = lya + lyb, nx = ncart(lxa) * ncart(lxb), ny = ncart(lya) * ncart(lyb);
+      // cost with X as bra vs Y as bra
+      const double cxy = px * (py * flops_prim(Lx, Lx + Ly, Y.cls) + flops_bra(X.cls, ny));
+      const double cyx = py * (px * flops_prim(Ly, Lx + Ly, X.cls) + flops_bra(Y.cls, nx));
+      Task t;
+      t.same = (x == y);
+      if (t.same || cxy <= cyx) {
+        t.bra = x;
+        t.ket = y;
+        t.cost = cxy;
+      } else {
+        t.bra = y;
+        t.ket = x;
+        t.cost = cyx;
+      }
+      int la, lb, lc, ld;
+      class_l(bins[t.bra].cls, la, lb);
+      class_l(bins[t.ket].cls, lc, ld);
+      t.scratch = scratch_doubles(la, lb, lc, ld);
+      int G = 1;
+      while (G < 32 && (32 / G) * t.scratch > 3072) G *= 2;
+      if (o.group_override > 0) {  // forced group size, raised where one warp's scratch would not fit
+        G = o.group_override;
+        while (G < 32 && (32 / G) * t.scratch > 24000) G *= 2;
+      }
+      t.G = G;
+      tasks.push_back(t);
+    }
+  std::stable_sort(tasks.begin(), tasks.end(), [](const Task &a, const Task &b) { return a.cost > b.cost; });
+
+  // tiers keyed by (G, scratch bucket)
+  struct TierKey {
+    int G, sb;
+    bool operator<(const TierKey &o2) const { return G != o2.G ? G < o2.G : sb < o2.sb; }
+    bool operator==(const TierKey &o2) const { return G == o2.G && sb == o2.sb; }
+  };
+  auto key_of = [](const Task &t) {
+    int sb = 0;
+    while ((1 << sb) < t.scratch) ++sb;
+    if (t.G < 32) sb = 0;  // one tier per G below a full warp
+    return TierKey{t.G, sb};
+  };
+  std::vector<TierKey> keys;
+  for (const Task &t : tasks) {
+    TierKey k = key_of(t);
+    if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
+  }
+  std::sort(keys.begin(), keys.end());
+  std::vector<Unit> all_units;
+  std::vector<int> unit_tier;
+  for (size_t ki = 0; ki < keys.size(); ++ki) {
+    Tier tier{};
+    tier.G = keys[ki].G;
+    int stride = 1;
+    const int chunk = (32 / tier.G) * 8;
+    const size_t first = all_units.size();
+    for (const Task &t : tasks) {
+      if (!(key_of(t) == keys[ki])) continue;
+      stride = std::max(stride, t.scratch);
+      const Bin &B = bins[t.bra], &K = bins[t.ket];
+      for (int i = B.begin; i < B.end; ++i) {
+        const double gi = st.G[i];
+        const int k0 = t.same ? i : K.begin;
+        // kets sorted by G descending: last index with G_i G_j >= tau
+        int lo = k0, hi = K.end;
+        while (lo < hi) {
+          const int mid = (lo + hi) / 2;
+          if (gi * st.G[mid] >= tau)
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+        for (int j = k0; j < lo; j += chunk) all_units.push_back(Unit{i, j, std::min(lo, j + chunk), 0});
+      }
+    }
+    if (stride % 2 == 0) ++stride;
+    tier.stride = stride;
+    tier.nunits = (int)(all_units.size() - first);
+    sp->tiers.push_back(tier);
+    for (size_t u = first; u < all_units.size(); ++u) unit_tier.push_back((int)ki);
+  }
+
+  // ---- upload compact data --------------------------------------------------
+  Unit *d_units = nullptr;
+  fock_status s = upload(st, all_units, &sp->d_block, sp->dev, &d_units, &sp->bytes, stream);
+  if (s != FOCK_OK) {
+    delete sp;
+    return s;
+  }
+  sp->dev.nshell = ns;
+  sp->dev.nbf = nbf;
+  size_t uoff = 0;
+  for (Tier &t : sp->tiers) {
+    t.d_units = d_units + uoff;
+    uoff += t.nunits;
+    ce = configure_tier(t);
+    if (ce != cudaSuccess) {
+      fock_shellpairs_free(sp);
+      return to_status(ce);
+    }
+  }
+  ce = cudaStreamSynchronize(stream);
+  if (ce != cudaSuccess) {
+    fock_shellpairs_free(sp);
+    return to_status(ce);
+  }
+  sp->h_sxyz = st.sxyz;
+  sp->h_sbf = st.sbf;
+  sp->h_sl = st.sl;
+  sp->h_ab = st.ab;
+  sp->h_G = st.G;
+  sp->h_prim = st.prim;
+  sp->h_cls = st.cls;
+  sp->h_units = std::move(all_units);
+  sp->h_unit_tier = std::move(unit_tier);
+  *out = sp;
+  return FOCK_OK;
+}
+
+fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double schwarz_thresh, double *J, double *K,
+                          cudaStream_t stream) {
+  if (!sp || !D || !J || !K) return FOCK_ERR_INVALID_ARG;
+  if (!(schwarz_thresh >= sp->tau_build) || !isfinite(schwarz_thresh)) return FOCK_ERR_INVALID_ARG;
+  const int ns = sp->nshell, n = sp->nbf;
+  const size_t nt = sp->tiers.size();
+  const size_t dsh_bytes = sizeof(double) * (size_t)ns * ns;
+  const size_t cnt_off = (dsh_bytes + 255) & ~(size_t)255;
+  char *scratch = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&scratch, cnt_off + sizeof(int) * (nt + 1), stream);
+  if (e != cudaSuccess) return to_status(e);
+  double *Dsh = (double *)scratch;
+  int *counters = (int *)(scratch + cnt_off);
+  e = cudaMemsetAsync(counters, 0, sizeof(int) * (nt + 1), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(J, 0, sizeof(double) * (size_t)n * n, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(K, 0, sizeof(double) * (size_t)n * n, stream);
+  if (e == cudaSuccess) e = launch_dprep(D, n, sp->dev.sbf, sp->dev.sl, ns, Dsh, stream);
+  for (size_t t = 0; t < nt && e == cudaSuccess; ++t)
+    e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, J, K, counters + t, stream);
+  if (e == cudaSuccess) e = launch_symmetrize(J, K, n, stream);
+  cudaError_t e2 = cudaFreeAsync(scratch, stream);
+  if (e == cudaSuccess) e = e2;
+  return to_status(e);
+}
+
+fock_status fock_build_jk_batched(const fock_shellpairs *const *bases, int32_t nmol, const double *const *D,
+                                  double schwarz_thresh, double *const *J, double *const *K, cudaStream_t stream) {
+  if (!bases || nmol < 0 || !D || !J || !K) return FOCK_ERR_INVALID_ARG;
+  for (int i = 0; i < nmol; ++i) {
+    fock_status s = fock_build_jk(bases[i], D[i], schwarz_thresh, J[i], K[i], stream);
+    if (s != FOCK_OK) return s;
+  }
+  return FOCK_OK;
+}
+
+fock_status fock_stream_status(cudaStream_t stream) {
+  int v = 0;
+  int rc = read_and_clear_status(stream, &v);
+  if (rc) return FOCK_ERR_CUDA;
+  return (fock_status)v;
+}
+
+fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, double schwarz_thresh, double out[8]) {
+  if (!sp || !D_host || !out) return FOCK_ERR_INVALID_ARG;
+  if (!(schwarz_thresh >= sp->tau_build)) return FOCK_ERR_INVALID_ARG;
+  const int ns = sp->nshell, n = sp->nbf;
+  std::vector<double> Dsh((size_t)ns * ns, 0.0);
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b) {
+      double mx = 0.0;
+      for (int i = 0; i < ncart(sp->h_sl[a]); ++i)
+        for (int j = 0; j < ncart(sp->h_sl[b]); ++j)
+          mx = std::max(mx, fabs(D_host[(size_t)(sp->h_sbf[a] + i) * n + sp->h_sbf[b] + j]));
+      Dsh[(size_t)a * ns + b] = mx;
+    }
+  double q1 = 0, e1 = 0, q2 = 0, e2 = 0, pq = 0, fl = 0;
+  const double tau = schwarz_thresh;
+  for (const Unit &u : sp->h_units) {
+    const int P = u.bra;
+    const int2 ab = sp->h_ab[P];
+    for (int Q = u.k0; Q < u.k1; ++Q) {
+      const int2 cd = sp->h_ab[Q];
+      const double g = sp->h_G[P] * sp->h_G[Q];
+      if (g < tau) continue;
+      const int la = sp->h_sl[ab.x], lb = sp->h_sl[ab.y], lc = sp->h_sl[cd.x], ld = sp->h_sl[cd.y];
+      const double ne = (double)ncart(la) * ncart(lb) * ncart(lc) * ncart(ld);
+      q1 += 1;
+      e1 += ne;
+      double dm = Dsh[(size_t)ab.x * ns + ab.y];
+      dm = std::max(dm, Dsh[(size_t)cd.x * ns + cd.y]);
+      dm = std::max(dm, Dsh[(size_t)ab.x * ns + cd.x]);
+      dm = std::max(dm, Dsh[(size_t)ab.x * ns + cd.y]);
+      dm = std::max(dm, Dsh[(size_t)ab.y * ns + cd.x]);
+      dm = std::max(dm, Dsh[(size_t)ab.y * ns + cd.y]);
+      if (g * dm < tau) continue;
+      q2 += 1;
+      e2 += ne;
+      const double np = (double)sp->h_prim[P].y * sp->h_prim[Q].y;
+      pq += np;
+      const FlopTable &ft = flop_table();
+      fl += np * ft.prim[sp->h_cls[P]][sp->h_cls[Q]] + sp->h_prim[P].y * ft.bra[sp->h_cls[P]][sp->h_cls[Q]] +
+            12.0 * ne;
+    }
+  }
+  double nprim = 0;
+  for (const int2 &p : sp->h_prim) nprim += p.y;
+  out[0] = q1;
+  out[1] = e1;
+  out[2] = q2;
+  out[3] = e2;
+  out[4] = pq;
+  out[5] = fl;
+  out[6] = nprim;
+  out[7] = (double)sp->h_ab.size();
+  return FOCK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Internal definitions of the GB300 J/K builder: constants, index helpers,
+// device-side data layout and the shell-pair handle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/fock.h"
+
+namespace fk {
+
+constexpr int LMAX = 3;             // f functions
+constexpr int LTOT = 4 * LMAX;      // largest total angular momentum of a quartet
+constexpr int NCLASS = 10;          // pair classes (la >= lb)
+constexpr int MAXPRIM = 8;          // primitives per shell
+constexpr int MAXCP = 100;          // Cartesian pairs of an (f,f) pair
+constexpr int NHMAX = 455;          // Hermite functions with t+u+v <= 12
+
+// Boys table: F_k(T_i), T_i = i*h, k = 0..BOYS_NORD-1, Taylor expansion of
+// order BOYS_TAYLOR about the nearest grid point; T >= BOYS_TMAX uses the
+// asymptotic form F_0 = sqrt(pi/T)/2 with upward recursion.
+constexpr int BOYS_TAYLOR = 8;                 // terms k = 0..7
+constexpr int BOYS_NORD = LTOT + BOYS_TAYLOR;  // orders 0..19
+constexpr double BOYS_H = 1.0 / 16.0;
+constexpr double BOYS_INVH = 16.0;
+constexpr double BOYS_TMAX = 64.0;
+constexpr int BOYS_NGRID = 1025;               // T_i for i = 0..1024
+
+__host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+__host__ __device__ constexpr int nherm(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+__host__ __device__ constexpr int pair_class(int la, int lb) { return la * (la + 1) / 2 + lb; }
+
+// Compact index of the Hermite (or Cartesian) exponent vector (t,u,v):
+// ordered by degree t+u+v, then t descending, then u descending.
+__host__ __device__ inline int hidx(int t, int u, int v) {
+  int d = t + u + v, r = d - t;
+  return d * (d + 1) * (d + 2) / 6 + r * (r + 1) / 2 + (r - u);
+}
+
+// Cartesian component i (0..ncart(l)-1) of a shell of angular momentum l.
+__host__ __device__ inline void cart_comp(int l, int i, int &x, int &y, int &z) {
+  int k = 0;
+  while (i > k) {
+    i -= k + 1;
+    ++k;
+  }
+  x = l - k;
+  y = k - i;
+  z = i;
+}
+
+// Primitive-pair centre and exponent (Px, Py, Pz, zeta), one 32-byte load.
+struct __align__(32) PZ {
+  double x, y, z, w;
+};
+
+// Per-class constant tables, copied into shared memory by the kernels
+// (16-byte aligned so its size is a whole number of 16-byte words).
+struct alignas(16) ClassTables {
+  int16_t eoff[NCLASS][MAXCP + 1];   // E offset of Cartesian pair k within a primitive pair block
+  int16_t nE[NCLASS];                // E doubles per primitive pair
+  uint8_t comp[LMAX + 1][10][3];     // Cartesian components per shell
+  uint8_t hvec[NHMAX][3];            // (t,u,v) of compact Hermite index
+};
+
+// Device view of a handle's pair data (plain pointers, passed by value).
+struct DevPairs {
+  // shells
+  const double *sxyz;  // [3*nshell]
+  const int *sbf;      // first basis function
+  const int *sl;       // angular momentum
+  // contracted pairs, sorted (class, contraction bucket, G descending)
+  const int2 *ab;      // canonical shells (la >= lb; a >= b when la == lb)
+  const double *G;     // Schwarz factor G_ab
+  const int2 *prim;    // (first primitive pair, count)
+  const int *cls;      // pair class
+  // primitive pairs
+  const PZ *pz;        // (Px, Py, Pz, zeta)
+  const double *U;     // U_P with contraction coefficients folded in
+  const int *eoff;     // offset of the primitive pair's E block
+  const double *E;     // Hermite coefficients (Cartesian normalisation folded in)
+  int nshell, nbf, npair;
+};
+
+// One unit of work: bra pair index, ket pair index range [k0, k1).
+struct Unit {
+  int bra, k0, k1, pad;
+};
+
+struct Tier {
+  int G;                // lanes per quartet
+  int stride;           // scratch doubles per group
+  int warps_per_block;
+  int blocks;           // persistent grid
+  size_t smem;          // dynamic shared memory per block
+  int nunits;
+  Unit *d_units;
+};
+
+}  // namespace fk
+
+struct fock_shellpairs {
+  int device = 0;
+  int nshell = 0, nbf = 0;
+  double tau_build = 0.0, prune_eps = 1e-3;
+  fock_opts opts{};
+  // host copies (for statistics and tests)
+  std::vector<double> h_sxyz;
+  std::vector<int> h_sbf, h_sl;
+  std::vector<int2> h_ab;
+  std::vector<double> h_G;
+  std::vector<int2> h_prim;
+  std::vector<int> h_cls;
+  std::vector<fk::Unit> h_units;      // all tiers, concatenated
+  std::vector<int> h_unit_tier;
+  // device allocations
+  void *d_block = nullptr;            // one allocation holding all pair arrays
+  fk::DevPairs dev{};
+  std::vector<fk::Tier> tiers;
+  size_t bytes = 0;
+};
+
+namespace fk {
+// host helpers (host_pairs.cpp)
+const ClassTables &class_tables();
+const std::vector<double> &boys_table();
+void boys_eval_host(int mmax, double T, double *F);
+void hermite_1d(int la, int lb, double p, double xpa, double xpb, double *E /*[4][4][7]*/);
+int hermite_count(int la, int lb);
+void hermite_pair(int la, int lb, double alpha, const double *A, double beta, const double *B,
+                  bool cart_norm, double *out);
+
+// device entry points (kernels.cu)
+cudaError_t upload_tables(cudaStream_t st);
+const double *dev_boys();
+const ClassTables *dev_class_tables();
+cudaError_t launch_schwarz(const DevPairs &dp, double *Gpair, double *Gprim, cudaStream_t st);
+cudaError_t launch_dprep(const double *D, int nbf, const int *sbf, const int *sl, int nshell,
+                         double *Dsh, cudaStream_t st);
+cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh,
+                           double tau, double *J, double *K, int *counter, cudaStream_t st);
+cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st);
+cudaError_t configure_tier(Tier &t);
+int read_and_clear_status(cudaStream_t st, int *status);
+}  // namespace fk

@@ -1,0 +1,549 @@
+// GB300 (sm_103a) kernels of the J/K build.
+//
+// Integral scheme: McMurchie-Davidson (arXiv:2407.21445 Sec. 4.1, Eqs. MD
+// def, EabP def1-3): a primitive quartet is
+//   [ab|cd] = sum_p sum_q E^{ab}_p (-1)^{|q|} R_{p+q} E^{cd}_q ,
+// R_{tuv} from the Hermite recursion R^{(n)}_{t+1,u,v} = t R^{(n+1)}_{t-1,u,v}
+// + X_PQ R^{(n+1)}_{tuv} seeded by R^{(n)}_{000} = pref (-2 alpha)^n F_n(T),
+// pref = U_P U_Q 2 sqrt(alpha/pi), alpha = zeta eta / (zeta + eta),
+// T = alpha |P-Q|^2 (the paper's garbled seed read this way).
+//
+// Work decomposition: a "group" of G lanes (G = 1..32, a power of two, chosen
+// per class pair) owns one contracted shell quartet (ab|cd) at a time.  For
+// each bra primitive pair it accumulates over the ket primitive pairs the
+// half-transformed Y[p][cd] = sum_q (-1)^{|q|} E^{cd}_q R_{p+q}, then applies
+// the bra transform ERI[ab][cd] += sum_p E^{ab}_p Y[p][cd]; the contracted
+// ERIs are then digested with the density into the six J/K blocks of the
+// 8-fold permutational symmetry (Sec. 2.3, Sec. 3.2 "six Fock matrix
+// blocks").  The intermediates live in a per-group shared-memory scratch.
+// Groups of one warp take consecutive ket pairs of one bra pair from a work
+// unit; warps pull units from a global counter (persistent grid).
+//
+// GB300 executes FP64 at 1/64 of the FP32 rate, so the kernels are bound by
+// the FP64 pipe; index arithmetic, shared-memory traffic and FP32 work are
+// comparatively free and are spent freely to keep FP64 lanes busy.
+#include <math.h>
+#include <stdio.h>
+
+#include "fock_impl.h"
+
+namespace fk {
+
+__device__ int g_status = 0;  // sticky device status word (fock_status)
+
+static double *s_boys[64];
+static ClassTables *s_tabs[64];
+
+struct KArgs {
+  DevPairs dp;
+  const double *D;
+  const double *Dsh;
+  double tau;
+  double *J;
+  double *K;
+  const Unit *units;
+  int nunits;
+  int *counter;
+  int stride;
+  const double *boys;
+  const ClassTables *tabs;
+};
+
+static_assert(sizeof(ClassTables) % 16 == 0, "table copy uses whole 4-byte words");
+constexpr int TAB_BYTES = (int)sizeof(ClassTables);
+
+__device__ __forceinline__ void group_sync(unsigned mask, int G) {
+  if (G > 1) __syncwarp(mask);
+}
+
+// F_m(T) from the table: Taylor expansion about the nearest grid point,
+// coefficients tab[i][m][k] = F_{m+k}(T_i)/k!, evaluated by Horner in
+// x = T_i - T (|x| <= h/2).  Beyond BOYS_TMAX: F_0 = sqrt(pi/T)/2 and
+// F_m = F_{m-1} (2m-1)/(2T).
+__device__ __forceinline__ double boys_eval(const double *__restrict__ tab, int m, double T) {
+  if (T < BOYS_TMAX) {
+    int i = __double2int_rn(T * BOYS_INVH);
+    double x = (double)i * BOYS_H - T;
+    const double *c = tab + ((size_t)i * (LTOT + 1) + m) * BOYS_TAYLOR;
+    double f = __ldg(c + 7);
+#pragma unroll
+    for (int k = 6; k >= 0; --k) f = fma(f, x, __ldg(c + k));
+    return f;
+  }
+  double f = 0.5 * sqrt(3.141592653589793238 / T);
+  double h = 0.5 / T;
+  for (int k = 1; k <= m; ++k) f *= (2 * k - 1) * h;
+  return f;
+}
+
+// R^{(0)}_{tuv}, t+u+v <= L, into the returned buffer (one of R0/R1).
+// F must hold base values pref (-2alpha)^n F_n(T), n = 0..L; R0[0] = F[L].
+template <int G>
+__device__ __forceinline__ double *hermite_r(const ClassTables &ct, int L, double X, double Y, double Z,
+                                             const double *F, double *R0, double *R1, int gl,
+                                             unsigned gmask) {
+  double *cur = R0, *nxt = R1;
+  for (int n = L - 1; n >= 0; --n) {
+    int cnt = nherm(L - n);
+    for (int e = gl; e < cnt; e += G) {
+      double v;
+      if (e == 0) {
+        v = F[n];
+      } else {
+        int t = ct.hvec[e][0], u = ct.hvec[e][1], w = ct.hvec[e][2];
+        if (t > 0) {
+          v = X * cur[hidx(t - 1, u, w)];
+          if (t > 1) v = fma((double)(t - 1), cur[hidx(t - 2, u, w)], v);
+        } else if (u > 0) {
+          v = Y * cur[hidx(t, u - 1, w)];
+          if (u > 1) v = fma((double)(u - 1), cur[hidx(t, u - 2, w)], v);
+        } else {
+          v = Z * cur[hidx(t, u, w - 1)];
+          if (w > 1) v = fma((double)(w - 1), cur[hidx(t, u, w - 2)], v);
+        }
+      }
+      nxt[e] = v;
+    }
+    group_sync(gmask, G);
+    double *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  return cur;
+}
+
+template <int G>
+__device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int P, int Q, int gl,
+                        unsigned gmask) {
+  const DevPairs &dp = a.dp;
+  const int2 ab = dp.ab[P], cd = dp.ab[Q];
+  const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
+  const int ns = dp.nshell;
+  // density-weighted Schwarz screening over the six shell blocks (Sec. 3.2)
+  const double g = dp.G[P] * dp.G[Q];
+  const double *Ds = a.Dsh;
+  double dm = Ds[sA * ns + sB];
+  dm = fmax(dm, Ds[sC * ns + sD]);
+  dm = fmax(dm, Ds[sA * ns + sC]);
+  dm = fmax(dm, Ds[sA * ns + sD]);
+  dm = fmax(dm, Ds[sB * ns + sC]);
+  dm = fmax(dm, Ds[sB * ns + sD]);
+  if (g < a.tau || g * dm < a.tau) return;
+
+  const int cb = dp.cls[P], ck = dp.cls[Q];
+  const int la = dp.sl[sA], lb = dp.sl[sB], lc = dp.sl[sC], ld = dp.sl[sD];
+  const int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
+  const int nab = na * nb, ncd = nc * nd;
+  const int Lab = la + lb, Lcd = lc + ld, L = Lab + Lcd;
+  const int nhab = nherm(Lab), nhL = nherm(L);
+  double *eri = scr;
+  double *Yh = eri + nab * ncd;
+  double *R0 = Yh + nhab * ncd;
+  double *R1 = R0 + nhL;
+  double *F = R1 + nhL;
+
+  for (int i = gl; i < nab * ncd; i += G) eri[i] = 0.0;
+  const int2 pb = dp.prim[P], pk = dp.prim[Q];
+  for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
+    const PZ P4 = dp.pz[ip];
+    const double UP = dp.U[ip];
+    const double *EP = dp.E + dp.eoff[ip];
+    for (int i = gl; i < nhab * ncd; i += G) Yh[i] = 0.0;
+    for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
+      const PZ Q4 = dp.pz[jq];
+      const double UQ = dp.U[jq];
+      const double *EQ = dp.E + dp.eoff[jq];
+      const double p = P4.w, q = Q4.w;
+      const double alpha = p * q / (p + q);
+      const double X = P4.x - Q4.x, Yd = P4.y - Q4.y, Z = P4.z - Q4.z;
+      const double T = alpha * (X * X + Yd * Yd + Z * Z);
+      const double pref = UP * UQ * 1.1283791670955126 * sqrt(alpha);  // 2/sqrt(pi)
+      for (int m = gl; m <= L; m += G) {
+        double s = pref;
+        for (int k = 0; k < m; ++k) s *= -2.0 * alpha;
+        double v = s * boys_eval(a.boys, m, T);
+        F[m] = v;
+        if (m == L) R0[0] = v;
+      }
+      group_sync(gmask, G);
+      const double *R = hermite_r<G>(ct, L, X, Yd, Z, F, R0, R1, gl, gmask);
+      // ket transform, accumulated over ket primitives
+      for (int it = gl; it < nhab * ncd; it += G) {
+        const int ph = it / ncd, kc = it - ph * ncd;
+        const int tp = ct.hvec[ph][0], up = ct.hvec[ph][1], vp = ct.hvec[ph][2];
+        const int ic = kc / nd, id = kc - ic * nd;
+        const uint8_t *cc = ct.comp[lc][ic], *dd = ct.comp[ld][id];
+        const int Tx = cc[0] + dd[0], Ty = cc[1] + dd[1], Tz = cc[2] + dd[2];
+        const double *Eq = EQ + ct.eoff[ck][kc];
+        double acc = 0.0;
+        int e = 0;
+        for (int t = 0; t <= Tx; ++t)
+          for (int u = 0; u <= Ty; ++u)
+            for (int v = 0; v <= Tz; ++v, ++e) {
+              const double r = R[hidx(tp + t, up + u, vp + v)];
+              acc = ((t + u + v) & 1) ? fma(-Eq[e], r, acc) : fma(Eq[e], r, acc);
+            }
+        Yh[it] += acc;
+      }
+      group_sync(gmask, G);
+    }
+    // bra transform
+    for (int it = gl; it < nab * ncd; it += G) {
+      const int ka = it / ncd, kc = it - ka * ncd;
+      const int ia = ka / nb, ib = ka - ia * nb;
+      const uint8_t *ac = ct.comp[la][ia], *bc = ct.comp[lb][ib];
+      const int Tx = ac[0] + bc[0], Ty = ac[1] + bc[1], Tz = ac[2] + bc[2];
+      const double *Ep = EP + ct.eoff[cb][ka];
+      double acc = 0.0;
+      int e = 0;
+      for (int t = 0; t <= Tx; ++t)
+        for (int u = 0; u <= Ty; ++u)
+          for (int v = 0; v <= Tz; ++v, ++e) acc = fma(Ep[e], Yh[hidx(t, u, v) * ncd + kc], acc);
+      eri[it] += acc;
+    }
+    group_sync(gmask, G);
+  }
+
+  // digestion into J and K (Sec. 2.3 eight-fold symmetry; J = Jt + Jt^T and
+  // K = Kt + Kt^T are formed afterwards by the symmetrisation kernel)
+  double fac = 1.0;
+  if (sA == sB) fac *= 0.5;
+  if (sC == sD) fac *= 0.5;
+  if (P == Q) fac *= 0.5;
+  const int N = dp.nbf;
+  const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
+  const double *Dm = a.D;
+  const int n1 = nab, n2 = n1 + ncd, n3 = n2 + na * nc, n4 = n3 + na * nd, n5 = n4 + nb * nc,
+            n6 = n5 + nb * nd;
+  for (int o = gl; o < n6; o += G) {
+    double s = 0.0;
+    double *dst;
+    if (o < n1) {
+      const int ia = o / nb, ib = o - ia * nb;
+      const double *e = eri + (size_t)o * ncd;
+      for (int ic = 0; ic < nc; ++ic)
+        for (int id = 0; id < nd; ++id) s = fma(e[ic * nd + id], Dm[(size_t)(fc + ic) * N + fd + id], s);
+      dst = a.J + (size_t)(fa + ia) * N + fb + ib;
+      s *= 2.0;
+    } else if (o < n2) {
+      const int k = o - n1, ic = k / nd, id = k - ic * nd;
+      for (int ia = 0; ia < na; ++ia)
+        for (int ib = 0; ib < nb; ++ib) s = fma(eri[(ia * nb + ib) * ncd + k], Dm[(size_t)(fa + ia) * N + fb + ib], s);
+      dst = a.J + (size_t)(fc + ic) * N + fd + id;
+      s *= 2.0;
+    } else if (o < n3) {  // K_ac += (ab|cd) D_bd
+      const int k = o - n2, ia = k / nc, ic = k - ia * nc;
+      for (int ib = 0; ib < nb; ++ib)
+        for (int id = 0; id < nd; ++id)
+          s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fb + ib) * N + fd + id], s);
+      dst = a.K + (size_t)(fa + ia) * N + fc + ic;
+    } else if (o < n4) {  // K_ad += (ab|cd) D_bc
+      const int k = o - n3, ia = k / nd, id = k - ia * nd;
+      for (int ib = 0; ib < nb; ++ib)
+        for (int ic = 0; ic < nc; ++ic)
+          s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fb + ib) * N + fc + ic], s);
+      dst = a.K + (size_t)(fa + ia) * N + fd + id;
+    } else if (o < n5) {  // K_bc += (ab|cd) D_ad
+      const int k = o - n4, ib = k / nc, ic = k - ib * nc;
+      for (int ia = 0; ia < na; ++ia)
+        for (int id = 0; id < nd; ++id)
+          s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fa + ia) * N + fd + id], s);
+      dst = a.K + (size_t)(fb + ib) * N + fc + ic;
+    } else {  // K_bd += (ab|cd) D_ac
+      const int k = o - n5, ib = k / nd, id = k - ib * nd;
+      for (int ia = 0; ia < na; ++ia)
+        for (int ic = 0; ic < nc; ++ic)
+          s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fa + ia) * N + fc + ic], s);
+      dst = a.K + (size_t)(fb + ib) * N + fd + id;
+    }
+    atomicAdd(dst, fac * s);
+  }
+  group_sync(gmask, G);
+}
+
+template <int G>
+__global__ void __launch_bounds__(128) k_jk(KArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  {
+    const int *src = reinterpret_cast<const int *>(a.tabs);
+    int *dst = reinterpret_cast<int *>(smem_raw);
+    for (int i = threadIdx.x; i < (int)(sizeof(ClassTables) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const ClassTables &ct = *reinterpret_cast<const ClassTables *>(smem_raw);
+  double *scr_base = reinterpret_cast<double *>(smem_raw + TAB_BYTES);
+  constexpr int NG = 32 / G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / G, gl = lane - grp * G;
+  double *scr = scr_base + (size_t)(warp * NG + grp) * a.stride;
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(a.counter, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= a.nunits) break;
+    const Unit un = a.units[u];
+    for (int Q = un.k0 + grp; Q < un.k1; Q += NG) quartet<G>(a, ct, scr, un.bra, Q, gl, gmask);
+  }
+}
+
+// Schwarz factors from diagonal integrals (Eqs. cauchy-schwarz 1, 2): one
+// warp per contracted pair; lanes own Cartesian pairs kc; for every primitive
+// quartet [ij|ij] ... all (i,j): the diagonal (kc|kc) element is
+// sum_p E^i_p sum_q (-1)^{|q|} E^j_q R_{p+q}.
+__global__ void __launch_bounds__(128) k_schwarz(DevPairs dp, const double *boys, const ClassTables *tabs,
+                                                 double *Gpair, double *Gprim) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  {
+    const int *src = reinterpret_cast<const int *>(tabs);
+    int *dst = reinterpret_cast<int *>(smem_raw);
+    for (int i = threadIdx.x; i < (int)(sizeof(ClassTables) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const ClassTables &ct = *reinterpret_cast<const ClassTables *>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double *scr = reinterpret_cast<double *>(smem_raw + TAB_BYTES) + warp * (2 * NHMAX + LTOT + 2);
+  double *R0 = scr, *R1 = scr + NHMAX, *F = scr + 2 * NHMAX;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int P = blockIdx.x * (blockDim.x >> 5) + warp; P < dp.npair; P += nw) {
+    const int2 ab = dp.ab[P];
+    const int la = dp.sl[ab.x], lb = dp.sl[ab.y], c = dp.cls[P];
+    const int nb = ncart(lb), nab = ncart(la) * nb, L = 2 * (la + lb);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int2 pr = dp.prim[P];
+    for (int i = pr.x; i < pr.x + pr.y; ++i) {
+      const PZ P4 = dp.pz[i];
+      for (int j = pr.x; j < pr.x + pr.y; ++j) {
+        const PZ Q4 = dp.pz[j];
+        const double p = P4.w, q = Q4.w, alpha = p * q / (p + q);
+        const double X = P4.x - Q4.x, Y = P4.y - Q4.y, Z = P4.z - Q4.z;
+        const double T = alpha * (X * X + Y * Y + Z * Z);
+        const double pref = dp.U[i] * dp.U[j] * 1.1283791670955126 * sqrt(alpha);
+        for (int m = lane; m <= L; m += 32) {
+          double s = pref;
+          for (int k = 0; k < m; ++k) s *= -2.0 * alpha;
+          double v = s * boys_eval(boys, m, T);
+          F[m] = v;
+          if (m == L) R0[0] = v;
+        }
+        __syncwarp();
+        const double *R = hermite_r<32>(ct, L, X, Y, Z, F, R0, R1, lane, 0xffffffffu);
+        double pm = 0.0;
+        for (int r = 0; r < 4; ++r) {
+          const int kc = lane + 32 * r;
+          if (kc >= nab) break;
+          const int ia = kc / nb, ib = kc - ia * nb;
+          const uint8_t *ac = ct.comp[la][ia], *bc = ct.comp[lb][ib];
+          const int Tx = ac[0] + bc[0], Ty = ac[1] + bc[1], Tz = ac[2] + bc[2];
+          const double *Ei = dp.E + dp.eoff[i] + ct.eoff[c][kc];
+          const double *Ej = dp.E + dp.eoff[j] + ct.eoff[c][kc];
+          double v = 0.0;
+          int e1 = 0;
+          for (int t1 = 0; t1 <= Tx; ++t1)
+            for (int u1 = 0; u1 <= Ty; ++u1)
+              for (int v1 = 0; v1 <= Tz; ++v1, ++e1) {
+                double inner = 0.0;
+                int e2 = 0;
+                for (int t2 = 0; t2 <= Tx; ++t2)
+                  for (int u2 = 0; u2 <= Ty; ++u2)
+                    for (int v2 = 0; v2 <= Tz; ++v2, ++e2) {
+                      const double rr = R[hidx(t1 + t2, u1 + u2, v1 + v2)];
+                      inner = ((t2 + u2 + v2) & 1) ? fma(-Ej[e2], rr, inner) : fma(Ej[e2], rr, inner);
+                    }
+                v = fma(Ei[e1], inner, v);
+              }
+          acc[r] += v;
+          pm = fmax(pm, fabs(v));
+        }
+        if (i == j) {
+          for (int o = 16; o > 0; o >>= 1) pm = fmax(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+          if (lane == 0) Gprim[i] = sqrt(pm);
+        }
+        __syncwarp();
+      }
+    }
+    double mx = 0.0;
+    for (int r = 0; r < 4; ++r)
+      if (lane + 32 * r < nab) mx = fmax(mx, acc[r]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) Gpair[P] = sqrt(fmax(mx, 0.0));
+  }
+}
+
+// Shell-block maxima |D| (Sec. 3.2 density screening) and a finiteness check.
+__global__ void k_dprep(const double *__restrict__ D, int N, const int *__restrict__ sbf,
+                        const int *__restrict__ sl, int ns, double *__restrict__ Dsh) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ns * ns) return;
+  const int a = idx / ns, b = idx - a * ns;
+  const int fa = sbf[a], fb = sbf[b], na = ncart(sl[a]), nb = ncart(sl[b]);
+  double mx = 0.0;
+  bool bad = false;
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < nb; ++j) {
+      const double v = D[(size_t)(fa + i) * N + fb + j];
+      if (!isfinite(v)) bad = true;
+      mx = fmax(mx, fabs(v));
+    }
+  if (bad) atomicCAS(&g_status, 0, (int)FOCK_ERR_NONFINITE);
+  Dsh[idx] = bad ? INFINITY : mx;
+}
+
+// M <- M + M^T in place, for J (z = 0) and K (z = 1).
+__global__ void k_symmetrize(double *J, double *K, int n) {
+  double *M = blockIdx.z == 0 ? J : K;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n || i > j) return;
+  if (i == j) {
+    M[(size_t)i * n + i] *= 2.0;
+  } else {
+    const double s = M[(size_t)i * n + j] + M[(size_t)j * n + i];
+    M[(size_t)i * n + j] = s;
+    M[(size_t)j * n + i] = s;
+  }
+}
+
+// --------------------------------------------------------------------------
+// host-side launch helpers
+// --------------------------------------------------------------------------
+
+cudaError_t upload_tables(cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (s_boys[dev] && s_tabs[dev]) return cudaSuccess;
+  const std::vector<double> &bt = boys_table();
+  double *b = nullptr;
+  ClassTables *t = nullptr;
+  if ((e = cudaMalloc(&b, bt.size() * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&t, sizeof(ClassTables))) != cudaSuccess) {
+    cudaFree(b);
+    return e;
+  }
+  e = cudaMemcpyAsync(b, bt.data(), bt.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t, &class_tables(), sizeof(ClassTables), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(b);
+    cudaFree(t);
+    return e;
+  }
+  s_boys[dev] = b;
+  s_tabs[dev] = t;
+  return cudaSuccess;
+}
+
+const double *dev_boys() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return s_boys[dev];
+}
+const ClassTables *dev_class_tables() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return s_tabs[dev];
+}
+
+cudaError_t launch_schwarz(const DevPairs &dp, double *Gpair, double *Gprim, cudaStream_t st) {
+  if (dp.npair == 0) return cudaSuccess;
+  const size_t smem = TAB_BYTES + 4 * (2 * NHMAX + LTOT + 2) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_schwarz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int blocks = (dp.npair + 3) / 4;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_schwarz<<<blocks, 128, smem, st>>>(dp, dev_boys(), dev_class_tables(), Gpair, Gprim);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dprep(const double *D, int nbf, const int *sbf, const int *sl, int nshell, double *Dsh,
+                         cudaStream_t st) {
+  const int n = nshell * nshell;
+  k_dprep<<<(n + 255) / 256, 256, 0, st>>>(D, nbf, sbf, sl, nshell, Dsh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st) {
+  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8, 2);
+  k_symmetrize<<<grd, blk, 0, st>>>(J, K, n);
+  return cudaGetLastError();
+}
+
+template <int G>
+static cudaError_t configure_g(Tier &t) {
+  const size_t per_warp = (size_t)(32 / G) * t.stride * sizeof(double);
+  int wpb = 4;
+  while (wpb > 1 && TAB_BYTES + wpb * per_warp > 227 * 1024) --wpb;
+  if (TAB_BYTES + wpb * per_warp > 227 * 1024) return cudaErrorInvalidValue;
+  t.warps_per_block = wpb;
+  t.smem = TAB_BYTES + wpb * per_warp;
+  cudaError_t e = cudaFuncSetAttribute(k_jk<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jk<G>, 32 * wpb, t.smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (per_sm < 1) per_sm = 1;
+  t.blocks = nsm * per_sm;
+  const int need = (t.nunits + wpb - 1) / wpb;
+  if (t.blocks > need) t.blocks = need > 0 ? need : 1;
+  return cudaSuccess;
+}
+
+cudaError_t configure_tier(Tier &t) {
+  switch (t.G) {
+    case 1: return configure_g<1>(t);
+    case 2: return configure_g<2>(t);
+    case 4: return configure_g<4>(t);
+    case 8: return configure_g<8>(t);
+    case 16: return configure_g<16>(t);
+    case 32: return configure_g<32>(t);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh, double tau,
+                           double *J, double *K, int *counter, cudaStream_t st) {
+  if (t.nunits == 0) return cudaSuccess;
+  KArgs a;
+  a.dp = dp;
+  a.D = D;
+  a.Dsh = Dsh;
+  a.tau = tau;
+  a.J = J;
+  a.K = K;
+  a.units = t.d_units;
+  a.nunits = t.nunits;
+  a.counter = counter;
+  a.stride = t.stride;
+  a.boys = dev_boys();
+  a.tabs = dev_class_tables();
+  const dim3 blk(32 * t.warps_per_block);
+  switch (t.G) {
+    case 1: k_jk<1><<<t.blocks, blk, t.smem, st>>>(a); break;
+    case 2: k_jk<2><<<t.blocks, blk, t.smem, st>>>(a); break;
+    case 4: k_jk<4><<<t.blocks, blk, t.smem, st>>>(a); break;
+    case 8: k_jk<8><<<t.blocks, blk, t.smem, st>>>(a); break;
+    case 16: k_jk<16><<<t.blocks, blk, t.smem, st>>>(a); break;
+    case 32: k_jk<32><<<t.blocks, blk, t.smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int read_and_clear_status(cudaStream_t st, int *status) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return (int)e;
+  int v = 0, zero = 0;
+  e = cudaMemcpyFromSymbol(&v, g_status, sizeof(int));
+  if (e != cudaSuccess) return (int)e;
+  e = cudaMemcpyToSymbol(g_status, &zero, sizeof(int));
+  if (e != cudaSuccess) return (int)e;
+  *status = v;
+  return 0;
+}
+
+}  // namespace fk

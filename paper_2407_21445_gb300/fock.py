@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libfock.so (include/fock.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; PyTorch supplies device
+memory and streams. Functions keep the C names. There is no CPU fallback: a
+missing or unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import _build
+
+FOCK_OK = 0
+FOCK_FP64, FOCK_MIXED = 0, 1
+STATUS_NAMES = ["FOCK_OK", "FOCK_ERR_INVALID_ARG", "FOCK_ERR_UNSUPPORTED_L", "FOCK_ERR_NONFINITE",
+                "FOCK_ERR_OOM", "FOCK_ERR_CUDA", "FOCK_ERR_TIMEOUT", "FOCK_ERR_NOT_CONVERGED"]
+
+
+class FockError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{where}: {name}")
+
+
+class fock_basis_desc(ctypes.Structure):
+    _fields_ = [("nshell", ctypes.c_int32), ("center", ctypes.c_void_p), ("l", ctypes.c_void_p),
+                ("nprim", ctypes.c_void_p), ("prim_off", ctypes.c_void_p), ("exps", ctypes.c_void_p),
+                ("coefs", ctypes.c_void_p), ("atom", ctypes.c_void_p)]
+
+
+class fock_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("fp32_cutoff", ctypes.c_double), ("prune_eps", ctypes.c_double),
+                ("group_override", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfock.so, building it in-tree first if it is absent or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libfock.so missing at {path}")
+            L = ctypes.CDLL(path)
+            p, d, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int32
+            L.fock_shellpairs_build.argtypes = [ctypes.POINTER(fock_basis_desc), ctypes.POINTER(fock_opts), d, p,
+                                                ctypes.POINTER(p)]
+            L.fock_shellpairs_build.restype = i
+            L.fock_shellpairs_free.argtypes = [p]
+            L.fock_shellpairs_free.restype = i
+            L.fock_nbasis.argtypes = [p]
+            L.fock_nbasis.restype = i
+            L.fock_kernels_per_build.argtypes = [p]
+            L.fock_kernels_per_build.restype = i
+            L.fock_build_jk.argtypes = [p, p, d, p, p, p]
+            L.fock_build_jk.restype = i
+            L.fock_build_jk_batched.argtypes = [p, i, p, d, p, p, p]
+            L.fock_build_jk_batched.restype = i
+            L.fock_work_stats.argtypes = [p, p, d, p]
+            L.fock_work_stats.restype = i
+            L.fock_stream_status.argtypes = [p]
+            L.fock_stream_status.restype = i
+            L.fock_status_string.argtypes = [i]
+            L.fock_status_string.restype = ctypes.c_char_p
+            L.fock_boys_table_info.argtypes = [p]
+            L.fock_boys_table_info.restype = i
+            L.fock_boys_host.argtypes = [i, d, p]
+            L.fock_boys_host.restype = i
+            L.fock_hermite_count.argtypes = [i, i]
+            L.fock_hermite_count.restype = i
+            L.fock_hermite_e.argtypes = [i, i, d, p, d, p, p]
+            L.fock_hermite_e.restype = i
+            _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Names of the entry points declared in include/fock.h."""
+    with open(os.path.join(_build.INCLUDE, "fock.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"FOCK_API\s+[\w\s\*]+?\b(fock_\w+)\s*\(", text)))
+
+
+def _check(rc: int, where: str):
+    if rc != FOCK_OK:
+        raise FockError(rc, where)
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _tensor_ptr(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _BasisArrays:
+    def __init__(self, basis: dict):
+        self.center = np.ascontiguousarray(basis["center"], dtype=np.float64)
+        self.l = np.ascontiguousarray(basis["l"], dtype=np.int32)
+        self.nprim = np.ascontiguousarray(basis["nprim"], dtype=np.int32)
+        self.prim_off = np.ascontiguousarray(basis["prim_off"], dtype=np.int32)
+        self.exps = np.ascontiguousarray(basis["exps"], dtype=np.float64)
+        self.coefs = np.ascontiguousarray(basis["coefs"], dtype=np.float64)
+        atom = basis.get("atom")
+        self.atom = None if atom is None else np.ascontiguousarray(atom, dtype=np.int32)
+        self.desc = fock_basis_desc(len(self.l), _np_ptr(self.center), _np_ptr(self.l), _np_ptr(self.nprim),
+                                    _np_ptr(self.prim_off), _np_ptr(self.exps), _np_ptr(self.coefs),
+                                    None if self.atom is None else _np_ptr(self.atom))
+
+
+def make_opts(precision=FOCK_FP64, fp32_cutoff=1e-5, prune_eps=1e-3, group_override=0) -> fock_opts:
+    o = fock_opts()
+    o.precision = precision
+    o.fp32_cutoff = fp32_cutoff
+    o.prune_eps = prune_eps
+    o.group_override = group_override
+    return o
+
+
+def fock_shellpairs_build(basis: dict, schwarz_thresh: float, opts: fock_opts | None = None, stream=None):
+    """Returns an opaque handle (ctypes.c_void_p); see include/fock.h."""
+    arr = _BasisArrays(basis)
+    out = ctypes.c_void_p()
+    rc = lib().fock_shellpairs_build(ctypes.byref(arr.desc), ctypes.byref(opts) if opts is not None else None,
+                                     float(schwarz_thresh), _stream_handle(stream), ctypes.byref(out))
+    _check(rc, "fock_shellpairs_build")
+    return out
+
+
+def fock_shellpairs_free(handle):
+    _check(lib().fock_shellpairs_free(handle), "fock_shellpairs_free")
+
+
+def fock_nbasis(handle) -> int:
+    return int(lib().fock_nbasis(handle))
+
+
+def fock_kernels_per_build(handle) -> int:
+    return int(lib().fock_kernels_per_build(handle))
+
+
+def fock_build_jk(handle, D, schwarz_thresh: float, J, K, stream=None):
+    rc = lib().fock_build_jk(handle, _tensor_ptr(D, "D"), float(schwarz_thresh), _tensor_ptr(J, "J"),
+                             _tensor_ptr(K, "K"), _stream_handle(stream))
+    _check(rc, "fock_build_jk")
+
+
+def fock_build_jk_batched(handles, Ds, schwarz_thresh: float, Js, Ks, stream=None):
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    Dp = (ctypes.c_void_p * n)(*[_tensor_ptr(x, "D").value for x in Ds])
+    Jp = (ctypes.c_void_p * n)(*[_tensor_ptr(x, "J").value for x in Js])
+    Kp = (ctypes.c_void_p * n)(*[_tensor_ptr(x, "K").value for x in Ks])
+    rc = lib().fock_build_jk_batched(H, n, Dp, float(schwarz_thresh), Jp, Kp, _stream_handle(stream))
+    _check(rc, "fock_build_jk_batched")
+
+
+def fock_work_stats(handle, D_host: np.ndarray, schwarz_thresh: float) -> dict:
+    D_host = np.ascontiguousarray(D_host, dtype=np.float64)
+    out = np.zeros(8)
+    _check(lib().fock_work_stats(handle, _np_ptr(D_host), float(schwarz_thresh), _np_ptr(out)), "fock_work_stats")
+    keys = ["quartets_schwarz", "eris_schwarz", "quartets_evaluated", "eris_evaluated", "prim_quartets",
+            "fp64_flops_model", "prim_pairs", "pairs"]
+    return {k: float(v) for k, v in zip(keys, out)}
+
+
+def fock_stream_status(stream=None) -> int:
+    return int(lib().fock_stream_status(_stream_handle(stream)))
+
+
+def fock_status_string(st: int) -> str:
+    return lib().fock_status_string(int(st)).decode()
+
+
+def fock_boys_table_info() -> dict:
+    out = np.zeros(4)
+    _check(lib().fock_boys_table_info(_np_ptr(out)), "fock_boys_table_info")
+    return dict(h=out[0], ngrid=int(out[1]), norders=int(out[2]), tmax=out[3])
+
+
+def fock_boys_host(mmax: int, T: float) -> np.ndarray:
+    F = np.zeros(mmax + 1)
+    _check(lib().fock_boys_host(int(mmax), float(T), _np_ptr(F)), "fock_boys_host")
+    return F
+
+
+def fock_hermite_count(la: int, lb: int) -> int:
+    return int(lib().fock_hermite_count(int(la), int(lb)))
+
+
+def fock_hermite_e(la: int, lb: int, alpha: float, A, beta: float, B) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    out = np.zeros(max(fock_hermite_count(la, lb), 1))
+    _check(lib().fock_hermite_e(int(la), int(lb), float(alpha), _np_ptr(A), float(beta), _np_ptr(B), _np_ptr(out)),
+           "fock_hermite_e")
+    return out
+
+
+class JKBuilder:
+    """Owns a shell-pair handle; builds J and K for device densities."""
+
+    def __init__(self, basis: dict, schwarz_thresh: float, opts: fock_opts | None = None, stream=None):
+        self.tau = float(schwarz_thresh)
+        self.handle = fock_shellpairs_build(basis, schwarz_thresh, opts, stream)
+        self.nbf = fock_nbasis(self.handle)
+
+    def build(self, D, J=None, K=None, tau=None, stream=None):
+        import torch
+        if J is None:
+            J = torch.empty_like(D)
+        if K is None:
+            K = torch.empty_like(D)
+        fock_build_jk(self.handle, D, self.tau if tau is None else tau, J, K, stream)
+        return J, K
+
+    def stats(self, D_host, tau=None) -> dict:
+        return fock_work_stats(self.handle, D_host, self.tau if tau is None else tau)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            fock_shellpairs_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
