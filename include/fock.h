@@ -130,7 +130,10 @@ FOCK_API int32_t fock_nbasis(const fock_shellpairs *sp);
  * the stream-ordered allocator (cudaMallocAsync) and released on the stream.
  * Errors (synchronous): FOCK_ERR_INVALID_ARG (null pointers, threshold below
  * the build threshold), FOCK_ERR_OOM, FOCK_ERR_CUDA.  A NaN/Inf in D sets
- * FOCK_ERR_NONFINITE in the status word (fock_stream_status).
+ * FOCK_ERR_NONFINITE in the status word (fock_stream_status).  With the
+ * environment variable FOCK_SYNC_CHECK=1 every launch is followed by a
+ * stream synchronisation so that a failure names its kernel
+ * (fock_last_error); that mode is for diagnosis only.
  */
 FOCK_API fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double schwarz_thresh,
                           double *J, double *K, cudaStream_t stream);
@@ -171,6 +174,16 @@ FOCK_API int32_t fock_kernels_per_build(const fock_shellpairs *sp);
 /* Synchronise the stream, return and clear the device status word
  * (FOCK_OK if no device-side error was recorded). */
 FOCK_API fock_status fock_stream_status(cudaStream_t stream);
+
+/* Description of the most recent CUDA runtime failure seen by the library
+ * on the calling thread ("" if none): the failing step and the CUDA error
+ * name.  Static thread-local storage, overwritten by the next failure. */
+FOCK_API const char *fock_last_error(void);
+
+/* Diagnostic word of a library built with -DFOCK_BOUNDS_CHECK: out[0] is
+ * the site of the first failed device-side bounds check (0 = none), out[1]
+ * the offending value.  Always {0, 0} in a normal build.  Synchronous. */
+FOCK_API fock_status fock_debug_bounds(int64_t out[2]);
 
 /* Human-readable name of a status code (static storage). */
 FOCK_API const char *fock_status_string(fock_status st);

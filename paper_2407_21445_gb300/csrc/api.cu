@@ -1,6 +1,8 @@
 // C-ABI entry points of the J/K builder (declared in include/fock.h) and the
 // shell-pair handle construction.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -43,10 +45,22 @@ struct Packer {
   }
 };
 
-fock_status to_status(cudaError_t e) {
+thread_local char g_last_error[256] = "";
+
+fock_status to_status(cudaError_t e, const char *where = "cuda") {
   if (e == cudaSuccess) return FOCK_OK;
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return FOCK_ERR_OOM;
   return FOCK_ERR_CUDA;
+}
+
+bool sync_check() {
+  static int v = -1;
+  if (v < 0) {
+    const char *s = getenv("FOCK_SYNC_CHECK");
+    v = (s && s[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
 }
 
 // Scratch (doubles) one group needs for a quartet of bra class cb, ket class ck.
@@ -180,6 +194,8 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   dp.eoff = (const int *)(d + o_eoff);
   dp.E = (const double *)(d + o_E);
   dp.npair = (int)st.ab.size();
+  dp.nprim_total = (int)st.pz.size();
+  dp.nE_total = (long long)st.E.size();
   if (d_units) *d_units = (Unit *)(d + o_units);
   *base = d;
   if (bytes) *bytes = total;
@@ -189,6 +205,17 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
 }  // namespace
 
 extern "C" {
+
+const char *fock_last_error(void) { return g_last_error; }
+
+fock_status fock_debug_bounds(int64_t out[2]) {
+  if (!out) return FOCK_ERR_INVALID_ARG;
+  long long v[2] = {0, 0};
+  if (read_bounds(v)) return FOCK_ERR_CUDA;
+  out[0] = v[0];
+  out[1] = v[1];
+  return FOCK_OK;
+}
 
 const char *fock_status_string(fock_status st) {
   switch (st) {
@@ -351,7 +378,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     cudaFree(base);
     if (ce != cudaSuccess) {
       delete sp;
-      return to_status(ce);
+      return to_status(ce, "Schwarz kernel");
     }
   }
 
@@ -517,7 +544,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     ce = configure_tier(t);
     if (ce != cudaSuccess) {
       fock_shellpairs_free(sp);
-      return to_status(ce);
+      return to_status(ce, "configure_tier");
     }
   }
   ce = cudaStreamSynchronize(stream);
@@ -551,16 +578,34 @@ fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double sch
   if (e != cudaSuccess) return to_status(e);
   double *Dsh = (double *)scratch;
   int *counters = (int *)(scratch + cnt_off);
+  const bool chk = sync_check();
+  const char *where = "memset";
   e = cudaMemsetAsync(counters, 0, sizeof(int) * (nt + 1), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(J, 0, sizeof(double) * (size_t)n * n, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(K, 0, sizeof(double) * (size_t)n * n, stream);
-  if (e == cudaSuccess) e = launch_dprep(D, n, sp->dev.sbf, sp->dev.sl, ns, Dsh, stream);
-  for (size_t t = 0; t < nt && e == cudaSuccess; ++t)
+  if (e == cudaSuccess) {
+    where = "k_dprep";
+    e = launch_dprep(D, n, sp->dev.sbf, sp->dev.sl, ns, Dsh, stream);
+    if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
+  }
+  static char tier_name[64];
+  for (size_t t = 0; t < nt && e == cudaSuccess; ++t) {
+    snprintf(tier_name, sizeof(tier_name), "k_jk tier %zu (G=%d, smem=%zu)", t, sp->tiers[t].G, sp->tiers[t].smem);
+    where = tier_name;
     e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, J, K, counters + t, stream);
-  if (e == cudaSuccess) e = launch_symmetrize(J, K, n, stream);
+    if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
+  }
+  if (e == cudaSuccess) {
+    where = "k_symmetrize";
+    e = launch_symmetrize(J, K, n, stream);
+    if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
+  }
   cudaError_t e2 = cudaFreeAsync(scratch, stream);
-  if (e == cudaSuccess) e = e2;
-  return to_status(e);
+  if (e == cudaSuccess) {
+    e = e2;
+    where = "cudaFreeAsync";
+  }
+  return to_status(e, where);
 }
 
 fock_status fock_build_jk_batched(const fock_shellpairs *const *bases, int32_t nmol, const double *const *D,

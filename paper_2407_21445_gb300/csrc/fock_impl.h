@@ -82,6 +82,8 @@ struct DevPairs {
   const int *eoff;     // offset of the primitive pair's E block
   const double *E;     // Hermite coefficients (Cartesian normalisation folded in)
   int nshell, nbf, npair;
+  int nprim_total;
+  long long nE_total;
 };
 
 // One unit of work: bra pair index, ket pair index range [k0, k1).
@@ -144,4 +146,5 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
 cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st);
 cudaError_t configure_tier(Tier &t);
 int read_and_clear_status(cudaStream_t st, int *status);
+int read_bounds(long long out[2]);
 }  // namespace fk

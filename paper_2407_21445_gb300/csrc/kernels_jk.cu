@@ -31,11 +31,32 @@ namespace fk {
 
 __device__ int g_status = 0;  // sticky device status word (fock_status)
 
+// Diagnostic bounds checks (compiled in with -DFOCK_BOUNDS_CHECK): a failed
+// check records its site and the offending value in g_bounds and skips the
+// quartet instead of touching memory.
+__device__ long long g_bounds[2] = {0, 0};
+#ifdef FOCK_BOUNDS_CHECK
+#define FK_CHECK(cond, site, val)                                          \
+  do {                                                                     \
+    if (!(cond)) {                                                         \
+      if (atomicCAS((unsigned long long *)&g_bounds[0], 0ull, (unsigned long long)(site)) == 0ull) \
+        g_bounds[1] = (long long)(val);                                    \
+      return;                                                              \
+    }                                                                      \
+  } while (0)
+#else
+#define FK_CHECK(cond, site, val) \
+  do {                            \
+  } while (0)
+#endif
+
 static double *s_boys[64];
 static ClassTables *s_tabs[64];
 
 struct KArgs {
   DevPairs dp;
+  int nprimtot;
+  long long nEtot;
   const double *D;
   const double *Dsh;
   double tau;
@@ -136,6 +157,15 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
   const int nab = na * nb, ncd = nc * nd;
   const int Lab = la + lb, Lcd = lc + ld, L = Lab + Lcd;
   const int nhab = nherm(Lab), nhL = nherm(L);
+  FK_CHECK(nab * ncd + nhab * ncd + 2 * nhL + L + 1 <= a.stride, 1, a.stride);
+  FK_CHECK(P >= 0 && P < dp.npair && Q >= 0 && Q < dp.npair, 2, Q);
+  FK_CHECK(dp.prim[P].x >= 0 && dp.prim[P].x + dp.prim[P].y <= a.nprimtot, 3, dp.prim[P].x);
+  FK_CHECK(dp.prim[Q].x >= 0 && dp.prim[Q].x + dp.prim[Q].y <= a.nprimtot, 4, dp.prim[Q].x);
+  FK_CHECK(dp.eoff[dp.prim[P].x + dp.prim[P].y - 1] + ct.nE[cb] <= a.nEtot, 5, cb);
+  FK_CHECK(dp.eoff[dp.prim[Q].x + dp.prim[Q].y - 1] + ct.nE[ck] <= a.nEtot, 6, ck);
+  FK_CHECK(dp.sbf[sA] + na <= dp.nbf && dp.sbf[sB] + nb <= dp.nbf && dp.sbf[sC] + nc <= dp.nbf &&
+               dp.sbf[sD] + nd <= dp.nbf, 7, sA);
+  FK_CHECK(L <= LTOT && nab <= MAXCP && ncd <= MAXCP, 8, L);
   double *eri = scr;
   double *Yh = eri + nab * ncd;
   double *R0 = Yh + nhab * ncd;
@@ -158,6 +188,7 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
       const double X = P4.x - Q4.x, Yd = P4.y - Q4.y, Z = P4.z - Q4.z;
       const double T = alpha * (X * X + Yd * Yd + Z * Z);
       const double pref = UP * UQ * 1.1283791670955126 * sqrt(alpha);  // 2/sqrt(pi)
+      FK_CHECK(T >= 0.0 && T == T, 9, jq);
       for (int m = gl; m <= L; m += G) {
         double s = pref;
         for (int k = 0; k < m; ++k) s *= -2.0 * alpha;
@@ -508,8 +539,23 @@ cudaError_t configure_tier(Tier &t) {
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh, double tau,
                            double *J, double *K, int *counter, cudaStream_t st) {
   if (t.nunits == 0) return cudaSuccess;
+  // The dynamic shared-memory limit is a per-function attribute shared by
+  // every handle; raise it to this tier's need before launching.
+  cudaError_t ae = cudaSuccess;
+  switch (t.G) {
+    case 1: ae = cudaFuncSetAttribute(k_jk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
+    case 2: ae = cudaFuncSetAttribute(k_jk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
+    case 4: ae = cudaFuncSetAttribute(k_jk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
+    case 8: ae = cudaFuncSetAttribute(k_jk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
+    case 16: ae = cudaFuncSetAttribute(k_jk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
+    case 32: ae = cudaFuncSetAttribute(k_jk<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (ae != cudaSuccess) return ae;
   KArgs a;
   a.dp = dp;
+  a.nprimtot = dp.nprim_total;
+  a.nEtot = dp.nE_total;
   a.D = D;
   a.Dsh = Dsh;
   a.tau = tau;
@@ -532,6 +578,10 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+int read_bounds(long long out[2]) {
+  return (int)cudaMemcpyFromSymbol(out, g_bounds, 2 * sizeof(long long));
 }
 
 int read_and_clear_status(cudaStream_t st, int *status) {

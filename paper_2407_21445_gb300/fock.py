@@ -52,7 +52,8 @@ def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            checked = os.environ.get("FOCK_CHECKED_LIB") == "1"  # bounds-checked diagnostic build
+            path = _build.build(checked=checked)
             if not os.path.exists(path):
                 raise RuntimeError(f"libfock.so missing at {path}")
             L = ctypes.CDLL(path)
@@ -74,6 +75,10 @@ def lib() -> ctypes.CDLL:
             L.fock_work_stats.restype = i
             L.fock_stream_status.argtypes = [p]
             L.fock_stream_status.restype = i
+            L.fock_debug_bounds.argtypes = [p]
+            L.fock_debug_bounds.restype = i
+            L.fock_last_error.argtypes = []
+            L.fock_last_error.restype = ctypes.c_char_p
             L.fock_status_string.argtypes = [i]
             L.fock_status_string.restype = ctypes.c_char_p
             L.fock_boys_table_info.argtypes = [p]
@@ -97,7 +102,8 @@ def declared_symbols():
 
 def _check(rc: int, where: str):
     if rc != FOCK_OK:
-        raise FockError(rc, where)
+        detail = lib().fock_last_error().decode() if rc == 5 else ""
+        raise FockError(rc, f"{where} [{detail}]" if detail else where)
 
 
 def _np_ptr(a: np.ndarray):
@@ -193,6 +199,16 @@ def fock_work_stats(handle, D_host: np.ndarray, schwarz_thresh: float) -> dict:
 
 def fock_stream_status(stream=None) -> int:
     return int(lib().fock_stream_status(_stream_handle(stream)))
+
+
+def fock_debug_bounds():
+    out = np.zeros(2, dtype=np.int64)
+    _check(lib().fock_debug_bounds(_np_ptr(out)), "fock_debug_bounds")
+    return int(out[0]), int(out[1])
+
+
+def fock_last_error() -> str:
+    return lib().fock_last_error().decode()
 
 
 def fock_status_string(st: int) -> str:
