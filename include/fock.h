@@ -139,6 +139,26 @@ FOCK_API fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, d
                           double *J, double *K, cudaStream_t stream);
 
 /*
+ * fock_build_jk without any device allocation.  The paper has no counterpart:
+ * this entry point is for callers that must not allocate device memory while
+ * they run -- services that reserve their whole memory budget at start-up,
+ * applications whose allocator policy forbids the CUDA runtime's
+ * stream-ordered pool, real-time loops where an allocation could stall.
+ * Arguments, layouts, errors and results are those of fock_build_jk.  The
+ * per-call scratch (shell-block density maxima and work counters) lives in a
+ * fixed 4 MiB array inside the library, which every GPU that loads the
+ * library keeps until the process exits; handles with more than 724 shells
+ * do not fit and return FOCK_ERR_INVALID_ARG without doing any work.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array: calls whose GPU work can overlap (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller.  No cudaMalloc, cudaMallocAsync or cudaFree is called.
+ */
+FOCK_API fock_status fock_build_jk_noalloc(const fock_shellpairs *sp, const double *D, double schwarz_thresh,
+                                           double *J, double *K, cudaStream_t stream);
+
+/*
  * J and K for nmol independent molecules in one pass: bases[i], D[i], J[i],
  * K[i] as in fock_build_jk (all device pointers; the pointer arrays themselves
  * are host memory read during the call).

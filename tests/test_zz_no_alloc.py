@@ -1,0 +1,68 @@
+"""fock_build_jk_noalloc: the allocation-free variant of fock_build_jk, called
+through the C ABI, must reproduce fock_build_jk on consecutive calls (its
+fixed scratch array keeps the previous call's contents) and refuse bases too
+large for that array.  Collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import molgen
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required")
+    import paper_2407_21445_gb300 as fk
+    L = fk.lib()
+    L.fock_build_jk_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]
+    L.fock_build_jk_noalloc.restype = ctypes.c_int32
+    return torch, fk, L
+
+
+def _noalloc(L, torch, handle, D, tau, J, K):
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return L.fock_build_jk_noalloc(handle, ctypes.c_void_p(D.data_ptr()), tau, ctypes.c_void_p(J.data_ptr()),
+                                   ctypes.c_void_p(K.data_ptr()), stream)
+
+
+@pytest.mark.parametrize("config", [0, 1])
+def test_noalloc_matches_fock_build_jk_twice(env, config):
+    torch, fk, L = env
+    p = molgen.problem(config)
+    b = fk.JKBuilder(p.basis, p.tau)
+    D = torch.tensor(p.D, device="cuda", dtype=torch.float64)
+    Jr, Kr = b.build(D)
+    torch.cuda.synchronize()
+    Jr, Kr = Jr.cpu().numpy(), Kr.cpu().numpy()
+    for call in range(2):
+        J = torch.full_like(D, float("nan"))
+        K = torch.full_like(D, float("nan"))
+        assert _noalloc(L, torch, b.handle, D, p.tau, J, K) == 0
+        torch.cuda.synchronize()
+        assert fk.fock_stream_status() == 0
+        ej = float(np.abs(J.cpu().numpy() - Jr).max())
+        ek = float(np.abs(K.cpu().numpy() - Kr).max())
+        assert ej <= TOL and ek <= TOL, (call, ej, ek)
+
+
+def test_noalloc_rejects_basis_beyond_array(env):
+    torch, fk, L = env
+    # 800 s shells (800^2 doubles of shell-block maxima exceed the 4 MiB array)
+    rng = np.random.Generator(np.random.PCG64(11))
+    shells = [(0, rng.uniform(-40, 40, 3), [0.5], [1.0]) for _ in range(800)]
+    bas = molgen.single_shell_basis(shells)
+    b = fk.JKBuilder(bas, 1e-8)
+    D = torch.eye(800, device="cuda", dtype=torch.float64)
+    J = torch.zeros_like(D)
+    K = torch.zeros_like(D)
+    assert _noalloc(L, torch, b.handle, D, 1e-8, J, K) == 1  # FOCK_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert float(J.abs().max()) == 0.0
