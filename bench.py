@@ -42,13 +42,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--carbons", type=int, default=20, help="alkane length for --config 1 (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
 def workload_config(p, st):
-    return {"workload": "C20H42 zigzag alkane, 6-31G(d)-shaped synthetic basis" if p.meta.get("config") == 1
-            else p.name, "nbf": int(p.nbf), "nshell": int(len(p.basis["l"])), "schwarz_thresh": p.tau,
+    c = p.meta.get("carbons", 20)
+    return {"workload": f"C{c}H{2 * c + 2} zigzag alkane, 6-31G(d)-shaped synthetic basis"
+            if p.meta.get("config") == 1 else p.name, "nbf": int(p.nbf), "nshell": int(len(p.basis["l"])), "schwarz_thresh": p.tau,
             "screening": "Schwarz + six-block density (Sec. 3.2)", "precision": "fp64",
             "eris_per_step": int(st["eris_schwarz"]), "quartets_per_step": int(st["quartets_schwarz"]),
             "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
@@ -152,7 +154,7 @@ def run_reference(args, rank, world):
     import oracle
     if rank != 0:
         return
-    p = molgen.problem(args.config)
+    p = molgen.problem(args.config, carbons=args.carbons)
     cnt = oracle.count(p.basis, p.D, p.tau)
     t0 = time.perf_counter()
     oracle.jk_sample(p.basis, p.D, p.tau, 64)
@@ -200,7 +202,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    p = molgen.problem(args.config)
+    p = molgen.problem(args.config, carbons=args.carbons)
     builder = fk.JKBuilder(p.basis, p.tau)
     st = builder.stats(p.D)
     nk = fk.fock_kernels_per_build(builder.handle)

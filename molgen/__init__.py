@@ -313,21 +313,24 @@ CONFIG_NAMES = {
 }
 
 
-def problem(config: int, seed: int = 0) -> Problem:
-    """The seeded synthetic workload for config 0 (water trimer), 1 (C20H42)
-    or 2 ((H2O)64 sphere)."""
+def problem(config: int, seed: int = 0, carbons: int = 20) -> Problem:
+    """The seeded synthetic workload for config 0 (water trimer), 1 (C20H42,
+    or another zigzag alkane length via `carbons`) or 2 ((H2O)64 sphere)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     if config == 0:
         mol, tau = water_chain_cluster(3, rng), 1e-12
     elif config == 1:
-        mol, tau = alkane_zigzag(20), 1e-10
+        mol, tau = alkane_zigzag(carbons), 1e-10
     elif config == 2:
         mol, tau = water_sphere_cluster(64, rng), 1e-10
     else:
         raise ValueError(f"unknown config {config}")
     basis = make_basis(mol, basis_set("dz", seed))
     D = density(basis, seed)
-    return Problem(CONFIG_NAMES[config], mol, basis, D, tau, dict(config=config, seed=seed))
+    name = CONFIG_NAMES[config]
+    if config == 1 and carbons != 20:
+        name = name.replace("C20H42", f"C{carbons}H{2 * carbons + 2}")
+    return Problem(name, mol, basis, D, tau, dict(config=config, seed=seed, carbons=carbons))
 
 
 def custom_problem(mol: Molecule, kind="dz", seed=0, tau=1e-10, name="custom") -> Problem:
