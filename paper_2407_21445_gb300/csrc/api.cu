@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fock_impl.h"
+#include "kernels_reg.cuh"
 
 using namespace fk;
 
@@ -26,6 +27,7 @@ struct Staging {  // host arrays mirroring DevPairs
   std::vector<int2> prim;
   std::vector<int> cls;
   std::vector<PZ> pz;
+  std::vector<float4> pf;
   std::vector<double> U;
   std::vector<int> eoff;
   std::vector<double> E;
@@ -166,6 +168,7 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   const size_t o_prim = pk.add(st.prim.data(), st.prim.size() * sizeof(int2));
   const size_t o_cls = pk.add(st.cls.data(), st.cls.size() * sizeof(int));
   const size_t o_pz = pk.add(st.pz.data(), st.pz.size() * sizeof(PZ));
+  const size_t o_pf = pk.add(st.pf.data(), st.pf.size() * sizeof(float4));
   const size_t o_U = pk.add(st.U.data(), st.U.size() * sizeof(double));
   const size_t o_eoff = pk.add(st.eoff.data(), st.eoff.size() * sizeof(int));
   const size_t o_E = pk.add(st.E.data(), st.E.size() * sizeof(double));
@@ -190,6 +193,7 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   dp.prim = (const int2 *)(d + o_prim);
   dp.cls = (const int *)(d + o_cls);
   dp.pz = (const PZ *)(d + o_pz);
+  dp.pf = (const float4 *)(d + o_pf);
   dp.U = (const double *)(d + o_U);
   dp.eoff = (const int *)(d + o_eoff);
   dp.E = (const double *)(d + o_E);
@@ -339,7 +343,10 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
           const double p = al + be;
           const PZ pz{(al * A[0] + be * B[0]) / p, (al * A[1] + be * B[1]) / p, (al * A[2] + be * B[2]) / p, p};
           all.pz.push_back(pz);
-          all.U.push_back(cn[a][i] * cn[b][j] * pow(kPi / p, 1.5) * exp(-al * be / p * AB2));
+          all.pf.push_back(make_float4((float)pz.x, (float)pz.y, (float)pz.z, (float)p));
+          // U_P sqrt(zeta) (2/sqrt(pi))^(1/2), so that U_P U_Q 2 sqrt(alpha/pi) = Us_P Us_Q / sqrt(zeta + eta)
+          all.U.push_back(cn[a][i] * cn[b][j] * pow(kPi / p, 1.5) * exp(-al * be / p * AB2) * sqrt(p) *
+                          sqrt(2.0 / sqrt(kPi)));
           all.eoff.push_back((int)all.E.size());
           const size_t e0 = all.E.size();
           all.E.resize(e0 + ct.nE[pair_class(la, lb)]);
@@ -415,6 +422,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     st.prim.push_back(make_int2((int)st.pz.size(), r.nkeep));
     for (int i : kept_prims[P]) {
       st.pz.push_back(all.pz[i]);
+      st.pf.push_back(all.pf[i]);
       st.U.push_back(all.U[i]);
       st.eoff.push_back((int)st.E.size());
       const int n = ct.nE[all.cls[P]];
@@ -437,6 +445,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     bool same;
     double cost;   // per quartet estimate
     int G, scratch;
+    bool reg;      // served by a per-class register kernel
   };
   std::vector<Task> tasks;
   for (int x = 0; x < (int)bins.size(); ++x)
@@ -472,21 +481,27 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
         while (G < 32 && (32 / G) * t.scratch > 24000) G *= 2;
       }
       t.G = G;
+      t.reg = o.group_override == 0 && reg_class_pair(bins[t.bra].cls, bins[t.ket].cls);
       tasks.push_back(t);
     }
   std::stable_sort(tasks.begin(), tasks.end(), [](const Task &a, const Task &b) { return a.cost > b.cost; });
 
   // tiers keyed by (G, scratch bucket)
   struct TierKey {
-    int G, sb;
-    bool operator<(const TierKey &o2) const { return G != o2.G ? G < o2.G : sb < o2.sb; }
-    bool operator==(const TierKey &o2) const { return G == o2.G && sb == o2.sb; }
+    int G, sb, cb, ck;  // cb >= 0: register kernel of (bra class, ket class)
+    bool operator<(const TierKey &o2) const {
+      if (cb != o2.cb) return cb < o2.cb;
+      if (ck != o2.ck) return ck < o2.ck;
+      return G != o2.G ? G < o2.G : sb < o2.sb;
+    }
+    bool operator==(const TierKey &o2) const { return G == o2.G && sb == o2.sb && cb == o2.cb && ck == o2.ck; }
   };
-  auto key_of = [](const Task &t) {
+  auto key_of = [&bins](const Task &t) {
+    if (t.reg) return TierKey{1, 0, bins[t.bra].cls, bins[t.ket].cls};
     int sb = 0;
     while ((1 << sb) < t.scratch) ++sb;
     if (t.G < 32) sb = 0;  // one tier per G below a full warp
-    return TierKey{t.G, sb};
+    return TierKey{t.G, sb, -1, -1};
   };
   std::vector<TierKey> keys;
   for (const Task &t : tasks) {
@@ -499,6 +514,8 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
   for (size_t ki = 0; ki < keys.size(); ++ki) {
     Tier tier{};
     tier.G = keys[ki].G;
+    tier.reg_cb = keys[ki].cb;
+    tier.reg_ck = keys[ki].ck;
     int stride = 1;
     const int chunk = (32 / tier.G) * 8;
     const size_t first = all_units.size();

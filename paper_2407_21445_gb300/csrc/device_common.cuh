@@ -1,0 +1,150 @@
+// Device helpers shared by the J/K kernels.
+//
+// GB300 issues FP64 instructions at 1/64 of the FP32 rate, while integer and
+// FP32 work is plentiful.  These helpers therefore move everything that does
+// not need 53-bit precision (grid indices, branch decisions, initial
+// approximations) to FP32/integer units and keep the FP64 instruction count
+// per primitive quartet small.
+#pragma once
+
+#include "fock_impl.h"
+
+namespace fk {
+
+// Exact float -> double by bit manipulation on the integer units (valid for
+// positive normal floats, which is all it is used for).
+__device__ __forceinline__ double f2d_pos(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long e = ((u >> 23) & 0xffu) + (1023u - 127u);
+  const unsigned long long m = u & 0x7fffffu;
+  return __longlong_as_double((long long)((e << 52) | (m << 29)));
+}
+
+// 1/sqrt(s) for s > 0 in double precision: FP32 seed y0 = rsqrtf(s_f), then
+// one third-order Householder step of the Newton iteration for 1/sqrt
+// (error e = 1 - s y0^2, y = y0 (1 + e/2 + 3e^2/8)); the seed's relative
+// error ~3e-7 is cubed to ~3e-20, so the result is limited by FP64 rounding.
+// sf is s rounded to FP32 (computed by the caller on the FP32 units).
+__device__ __forceinline__ double rsqrt_nh(double s, float sf) {
+  const double y0 = f2d_pos(rsqrtf(sf));
+  const double t = s * y0;
+  const double e = fma(-t, y0, 1.0);
+  const double c = e * fma(e, 0.375, 0.5);
+  return fma(y0, c, y0);
+}
+
+// Quantities of one primitive quartet [ab|cd] used by every class.
+struct PrimQuartet {
+  double X, Y, Z;   // P - Q
+  double T;         // alpha |P - Q|^2
+  double m2a;       // -2 alpha
+  double pref;      // U_P U_Q 2 sqrt(alpha/pi)
+  int gi;           // Boys grid index (T < BOYS_TMAX) or -1 (asymptotic)
+  double Ti;        // grid abscissa i*h (exact)
+  float Tf;         // T on the FP32 units (seed of the asymptotic rsqrt)
+};
+
+// P4 = (Px, Py, Pz, zeta), Pf = the same in FP32, Us = U_P sqrt(zeta) (2/sqrt(pi))^(1/2).
+__device__ __forceinline__ PrimQuartet prim_quartet(const PZ &P4, const float4 &Pf, double UsP, const PZ &Q4,
+                                                    const float4 &Qf, double UsQ) {
+  PrimQuartet r;
+  const double s = P4.w + Q4.w;
+  const float sf = Pf.w + Qf.w;
+  const double rs = rsqrt_nh(s, sf);
+  r.pref = UsP * UsQ * rs;
+  const double alpha = (P4.w * Q4.w) * (rs * rs);
+  r.m2a = -2.0 * alpha;
+  r.X = P4.x - Q4.x;
+  r.Y = P4.y - Q4.y;
+  r.Z = P4.z - Q4.z;
+  r.T = alpha * fma(r.X, r.X, fma(r.Y, r.Y, r.Z * r.Z));
+  // grid decision on the FP32 units (an index off by one at a half-point
+  // still leaves |T - T_i| < h, well inside the Taylor error bound)
+  const float xf = Pf.x - Qf.x, yf = Pf.y - Qf.y, zf = Pf.z - Qf.z;
+  const float Tf = __fdividef(Pf.w * Qf.w, sf) * (xf * xf + yf * yf + zf * zf);
+  r.Tf = Tf;
+  if (Tf < (float)BOYS_TMAX) {
+    r.gi = __float2int_rn(Tf * (float)BOYS_INVH);
+    r.Ti = (r.gi == 0) ? 0.0 : f2d_pos((float)r.gi * (float)BOYS_H);
+  } else {
+    r.gi = -1;
+    r.Ti = 0.0;
+  }
+  return r;
+}
+
+// F_m(T) for one m from the table (Taylor about T_i, Horner in x = T_i - T).
+__device__ __forceinline__ double boys_taylor(const double *__restrict__ tab, int gi, int m, double x) {
+  const double *c = tab + ((size_t)gi * (LTOT + 1) + m) * BOYS_TAYLOR;
+  double f = __ldg(c + 7);
+#pragma unroll
+  for (int k = 6; k >= 0; --k) f = fma(f, x, __ldg(c + k));
+  return f;
+}
+
+// Seeds pref (-2 alpha)^m F_m(T), m = 0..L, into out[] (compile-time L).
+template <int L>
+__device__ __forceinline__ void boys_seeds(const double *__restrict__ tab, const PrimQuartet &q, double (&out)[L + 1]) {
+  if (q.gi >= 0) {
+    const double x = q.Ti - q.T;
+#pragma unroll
+    for (int m = 0; m <= L; ++m) out[m] = boys_taylor(tab, q.gi, m, x);
+  } else {
+    // asymptotic: F_0 = sqrt(pi/T)/2, F_m = F_{m-1} (m - 1/2) / T
+    const double rt = rsqrt_nh(q.T, q.Tf);
+    out[0] = 0.88622692545275801365 * rt;  // sqrt(pi)/2
+    const double it = rt * rt;
+#pragma unroll
+    for (int m = 1; m <= L; ++m) out[m] = out[m - 1] * ((m - 0.5) * it);
+  }
+  double c = q.pref;
+#pragma unroll
+  for (int m = 0; m <= L; ++m) {
+    out[m] *= c;
+    c *= q.m2a;
+  }
+}
+
+// Runtime-L variant for the group-cooperative kernel: lanes gl, gl+G, ...
+// write seeds m into F[]; the lane that writes m = L also writes R0[0].
+template <int G>
+__device__ __forceinline__ void boys_seeds_rt(const double *__restrict__ tab, const PrimQuartet &q, int L, double *F,
+                                              double *R0, int gl) {
+  if constexpr (G == 1) {
+    double c = q.pref, prev = 0.0;
+    const double x = q.Ti - q.T;
+    double rt = 0.0, it = 0.0;
+    if (q.gi < 0) {
+      rt = rsqrt_nh(q.T, q.Tf);
+      it = rt * rt;
+    }
+    for (int m = 0; m <= L; ++m) {
+      double f;
+      if (q.gi >= 0)
+        f = boys_taylor(tab, q.gi, m, x);
+      else
+        f = (m == 0) ? 0.88622692545275801365 * rt : prev * ((m - 0.5) * it);
+      prev = f;
+      F[m] = f * c;
+      c *= q.m2a;
+    }
+    R0[0] = F[L];
+  } else {
+  for (int m = gl; m <= L; m += G) {
+    double f;
+    if (q.gi >= 0) {
+      f = boys_taylor(tab, q.gi, m, q.Ti - q.T);
+    } else {
+      const double rt = rsqrt_nh(q.T, q.Tf), it = rt * rt;
+      f = 0.88622692545275801365 * rt;
+      for (int k = 1; k <= m; ++k) f *= (k - 0.5) * it;
+    }
+    double c = q.pref;
+    for (int k = 0; k < m; ++k) c *= q.m2a;
+    F[m] = f * c;
+    if (m == L) R0[0] = F[m];
+  }
+  }
+}
+
+}  // namespace fk

@@ -78,7 +78,8 @@ struct DevPairs {
   const int *cls;      // pair class
   // primitive pairs
   const PZ *pz;        // (Px, Py, Pz, zeta)
-  const double *U;     // U_P with contraction coefficients folded in
+  const float4 *pf;    // the same in FP32 (grid indices, seeds)
+  const double *U;     // U_P sqrt(zeta) (2/sqrt(pi))^(1/2): pref = U_P U_Q / sqrt(zeta + eta)
   const int *eoff;     // offset of the primitive pair's E block
   const double *E;     // Hermite coefficients (Cartesian normalisation folded in)
   int nshell, nbf, npair;
@@ -92,7 +93,9 @@ struct Unit {
 };
 
 struct Tier {
-  int G;                // lanes per quartet
+  int reg_cb = -1;      // >= 0: per-class register kernel for (bra class, ket class)
+  int reg_ck = -1;
+  int G;                // lanes per quartet (group kernel)
   int stride;           // scratch doubles per group
   int warps_per_block;
   int blocks;           // persistent grid

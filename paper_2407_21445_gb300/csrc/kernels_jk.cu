@@ -25,7 +25,9 @@
 #include <math.h>
 #include <stdio.h>
 
-#include "fock_impl.h"
+#include "device_common.cuh"
+#include "kargs.cuh"
+#include "reg_dispatch.h"
 
 namespace fk {
 
@@ -53,22 +55,7 @@ __device__ long long g_bounds[2] = {0, 0};
 static double *s_boys[64];
 static ClassTables *s_tabs[64];
 
-struct KArgs {
-  DevPairs dp;
-  int nprimtot;
-  long long nEtot;
-  const double *D;
-  const double *Dsh;
-  double tau;
-  double *J;
-  double *K;
-  const Unit *units;
-  int nunits;
-  int *counter;
-  int stride;
-  const double *boys;
-  const ClassTables *tabs;
-};
+
 
 static_assert(sizeof(ClassTables) % 16 == 0, "table copy uses whole 4-byte words");
 constexpr int TAB_BYTES = (int)sizeof(ClassTables);
@@ -77,28 +64,10 @@ __device__ __forceinline__ void group_sync(unsigned mask, int G) {
   if (G > 1) __syncwarp(mask);
 }
 
-// F_m(T) from the table: Taylor expansion about the nearest grid point,
-// coefficients tab[i][m][k] = F_{m+k}(T_i)/k!, evaluated by Horner in
-// x = T_i - T (|x| <= h/2).  Beyond BOYS_TMAX: F_0 = sqrt(pi/T)/2 and
-// F_m = F_{m-1} (2m-1)/(2T).
-__device__ __forceinline__ double boys_eval(const double *__restrict__ tab, int m, double T) {
-  if (T < BOYS_TMAX) {
-    int i = __double2int_rn(T * BOYS_INVH);
-    double x = (double)i * BOYS_H - T;
-    const double *c = tab + ((size_t)i * (LTOT + 1) + m) * BOYS_TAYLOR;
-    double f = __ldg(c + 7);
-#pragma unroll
-    for (int k = 6; k >= 0; --k) f = fma(f, x, __ldg(c + k));
-    return f;
-  }
-  double f = 0.5 * sqrt(3.141592653589793238 / T);
-  double h = 0.5 / T;
-  for (int k = 1; k <= m; ++k) f *= (2 * k - 1) * h;
-  return f;
-}
-
 // R^{(0)}_{tuv}, t+u+v <= L, into the returned buffer (one of R0/R1).
 // F must hold base values pref (-2alpha)^n F_n(T), n = 0..L; R0[0] = F[L].
+__constant__ double c_small[16] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15};
+
 template <int G>
 __device__ __forceinline__ double *hermite_r(const ClassTables &ct, int L, double X, double Y, double Z,
                                              const double *F, double *R0, double *R1, int gl,
@@ -114,13 +83,13 @@ __device__ __forceinline__ double *hermite_r(const ClassTables &ct, int L, doubl
         int t = ct.hvec[e][0], u = ct.hvec[e][1], w = ct.hvec[e][2];
         if (t > 0) {
           v = X * cur[hidx(t - 1, u, w)];
-          if (t > 1) v = fma((double)(t - 1), cur[hidx(t - 2, u, w)], v);
+          if (t > 1) v = fma(c_small[t - 1], cur[hidx(t - 2, u, w)], v);
         } else if (u > 0) {
           v = Y * cur[hidx(t, u - 1, w)];
-          if (u > 1) v = fma((double)(u - 1), cur[hidx(t, u - 2, w)], v);
+          if (u > 1) v = fma(c_small[u - 1], cur[hidx(t, u - 2, w)], v);
         } else {
           v = Z * cur[hidx(t, u, w - 1)];
-          if (w > 1) v = fma((double)(w - 1), cur[hidx(t, u, w - 2)], v);
+          if (w > 1) v = fma(c_small[w - 1], cur[hidx(t, u, w - 2)], v);
         }
       }
       nxt[e] = v;
@@ -139,17 +108,8 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
   const DevPairs &dp = a.dp;
   const int2 ab = dp.ab[P], cd = dp.ab[Q];
   const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
-  const int ns = dp.nshell;
   // density-weighted Schwarz screening over the six shell blocks (Sec. 3.2)
-  const double g = dp.G[P] * dp.G[Q];
-  const double *Ds = a.Dsh;
-  double dm = Ds[sA * ns + sB];
-  dm = fmax(dm, Ds[sC * ns + sD]);
-  dm = fmax(dm, Ds[sA * ns + sC]);
-  dm = fmax(dm, Ds[sA * ns + sD]);
-  dm = fmax(dm, Ds[sB * ns + sC]);
-  dm = fmax(dm, Ds[sB * ns + sD]);
-  if (g < a.tau || g * dm < a.tau) return;
+  if (screened(a, sA, sB, sC, sD, P, Q)) return;
 
   const int cb = dp.cls[P], ck = dp.cls[Q];
   const int la = dp.sl[sA], lb = dp.sl[sB], lc = dp.sl[sC], ld = dp.sl[sD];
@@ -176,28 +136,17 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
     const PZ P4 = dp.pz[ip];
+    const float4 Pf = dp.pf[ip];
     const double UP = dp.U[ip];
     const double *EP = dp.E + dp.eoff[ip];
     for (int i = gl; i < nhab * ncd; i += G) Yh[i] = 0.0;
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
-      const PZ Q4 = dp.pz[jq];
-      const double UQ = dp.U[jq];
       const double *EQ = dp.E + dp.eoff[jq];
-      const double p = P4.w, q = Q4.w;
-      const double alpha = p * q / (p + q);
-      const double X = P4.x - Q4.x, Yd = P4.y - Q4.y, Z = P4.z - Q4.z;
-      const double T = alpha * (X * X + Yd * Yd + Z * Z);
-      const double pref = UP * UQ * 1.1283791670955126 * sqrt(alpha);  // 2/sqrt(pi)
-      FK_CHECK(T >= 0.0 && T == T, 9, jq);
-      for (int m = gl; m <= L; m += G) {
-        double s = pref;
-        for (int k = 0; k < m; ++k) s *= -2.0 * alpha;
-        double v = s * boys_eval(a.boys, m, T);
-        F[m] = v;
-        if (m == L) R0[0] = v;
-      }
+      const PrimQuartet q = prim_quartet(P4, Pf, UP, dp.pz[jq], dp.pf[jq], dp.U[jq]);
+      FK_CHECK(q.T >= 0.0 && q.T == q.T && q.gi <= BOYS_NGRID - 1, 9, jq);
+      boys_seeds_rt<G>(a.boys, q, L, F, R0, gl);
       group_sync(gmask, G);
-      const double *R = hermite_r<G>(ct, L, X, Yd, Z, F, R0, R1, gl, gmask);
+      const double *R = hermite_r<G>(ct, L, q.X, q.Y, q.Z, F, R0, R1, gl, gmask);
       // ket transform, accumulated over ket primitives
       for (int it = gl; it < nhab * ncd; it += G) {
         const int ph = it / ncd, kc = it - ph * ncd;
@@ -206,7 +155,7 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
         const uint8_t *cc = ct.comp[lc][ic], *dd = ct.comp[ld][id];
         const int Tx = cc[0] + dd[0], Ty = cc[1] + dd[1], Tz = cc[2] + dd[2];
         const double *Eq = EQ + ct.eoff[ck][kc];
-        double acc = 0.0;
+        double acc = Yh[it];
         int e = 0;
         for (int t = 0; t <= Tx; ++t)
           for (int u = 0; u <= Ty; ++u)
@@ -214,7 +163,7 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
               const double r = R[hidx(tp + t, up + u, vp + v)];
               acc = ((t + u + v) & 1) ? fma(-Eq[e], r, acc) : fma(Eq[e], r, acc);
             }
-        Yh[it] += acc;
+        Yh[it] = acc;
       }
       group_sync(gmask, G);
     }
@@ -225,12 +174,12 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
       const uint8_t *ac = ct.comp[la][ia], *bc = ct.comp[lb][ib];
       const int Tx = ac[0] + bc[0], Ty = ac[1] + bc[1], Tz = ac[2] + bc[2];
       const double *Ep = EP + ct.eoff[cb][ka];
-      double acc = 0.0;
+      double acc = eri[it];
       int e = 0;
       for (int t = 0; t <= Tx; ++t)
         for (int u = 0; u <= Ty; ++u)
           for (int v = 0; v <= Tz; ++v, ++e) acc = fma(Ep[e], Yh[hidx(t, u, v) * ncd + kc], acc);
-      eri[it] += acc;
+      eri[it] = acc;
     }
     group_sync(gmask, G);
   }
@@ -244,6 +193,7 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
   const int N = dp.nbf;
   const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
   const double *Dm = a.D;
+  const double fac2 = 2.0 * fac;
   const int n1 = nab, n2 = n1 + ncd, n3 = n2 + na * nc, n4 = n3 + na * nd, n5 = n4 + nb * nc,
             n6 = n5 + nb * nd;
   for (int o = gl; o < n6; o += G) {
@@ -255,39 +205,43 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
       for (int ic = 0; ic < nc; ++ic)
         for (int id = 0; id < nd; ++id) s = fma(e[ic * nd + id], Dm[(size_t)(fc + ic) * N + fd + id], s);
       dst = a.J + (size_t)(fa + ia) * N + fb + ib;
-      s *= 2.0;
+      s *= fac2;
     } else if (o < n2) {
       const int k = o - n1, ic = k / nd, id = k - ic * nd;
       for (int ia = 0; ia < na; ++ia)
         for (int ib = 0; ib < nb; ++ib) s = fma(eri[(ia * nb + ib) * ncd + k], Dm[(size_t)(fa + ia) * N + fb + ib], s);
       dst = a.J + (size_t)(fc + ic) * N + fd + id;
-      s *= 2.0;
+      s *= fac2;
     } else if (o < n3) {  // K_ac += (ab|cd) D_bd
       const int k = o - n2, ia = k / nc, ic = k - ia * nc;
       for (int ib = 0; ib < nb; ++ib)
         for (int id = 0; id < nd; ++id)
           s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fb + ib) * N + fd + id], s);
       dst = a.K + (size_t)(fa + ia) * N + fc + ic;
+      s *= fac;
     } else if (o < n4) {  // K_ad += (ab|cd) D_bc
       const int k = o - n3, ia = k / nd, id = k - ia * nd;
       for (int ib = 0; ib < nb; ++ib)
         for (int ic = 0; ic < nc; ++ic)
           s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fb + ib) * N + fc + ic], s);
       dst = a.K + (size_t)(fa + ia) * N + fd + id;
+      s *= fac;
     } else if (o < n5) {  // K_bc += (ab|cd) D_ad
       const int k = o - n4, ib = k / nc, ic = k - ib * nc;
       for (int ia = 0; ia < na; ++ia)
         for (int id = 0; id < nd; ++id)
           s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fa + ia) * N + fd + id], s);
       dst = a.K + (size_t)(fb + ib) * N + fc + ic;
+      s *= fac;
     } else {  // K_bd += (ab|cd) D_ac
       const int k = o - n5, ib = k / nd, id = k - ib * nd;
       for (int ia = 0; ia < na; ++ia)
         for (int ic = 0; ic < nc; ++ic)
           s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fa + ia) * N + fc + ic], s);
       dst = a.K + (size_t)(fb + ib) * N + fd + id;
+      s *= fac;
     }
-    atomicAdd(dst, fac * s);
+    atomicAdd(dst, s);
   }
   group_sync(gmask, G);
 }
@@ -309,9 +263,7 @@ __global__ void __launch_bounds__(128) k_jk(KArgs a) {
   double *scr = scr_base + (size_t)(warp * NG + grp) * a.stride;
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
   for (;;) {
-    int u = 0;
-    if (lane == 0) u = atomicAdd(a.counter, 1);
-    u = __shfl_sync(0xffffffffu, u, 0);
+    const int u = next_unit(a.counter, lane);
     if (u >= a.nunits) break;
     const Unit un = a.units[u];
     for (int Q = un.k0 + grp; Q < un.k1; Q += NG) quartet<G>(a, ct, scr, un.bra, Q, gl, gmask);
@@ -344,21 +296,12 @@ __global__ void __launch_bounds__(128) k_schwarz(DevPairs dp, const double *boys
     const int2 pr = dp.prim[P];
     for (int i = pr.x; i < pr.x + pr.y; ++i) {
       const PZ P4 = dp.pz[i];
+      const float4 Pf = dp.pf[i];
       for (int j = pr.x; j < pr.x + pr.y; ++j) {
-        const PZ Q4 = dp.pz[j];
-        const double p = P4.w, q = Q4.w, alpha = p * q / (p + q);
-        const double X = P4.x - Q4.x, Y = P4.y - Q4.y, Z = P4.z - Q4.z;
-        const double T = alpha * (X * X + Y * Y + Z * Z);
-        const double pref = dp.U[i] * dp.U[j] * 1.1283791670955126 * sqrt(alpha);
-        for (int m = lane; m <= L; m += 32) {
-          double s = pref;
-          for (int k = 0; k < m; ++k) s *= -2.0 * alpha;
-          double v = s * boys_eval(boys, m, T);
-          F[m] = v;
-          if (m == L) R0[0] = v;
-        }
+        const PrimQuartet q = prim_quartet(P4, Pf, dp.U[i], dp.pz[j], dp.pf[j], dp.U[j]);
+        boys_seeds_rt<32>(boys, q, L, F, R0, lane);
         __syncwarp();
-        const double *R = hermite_r<32>(ct, L, X, Y, Z, F, R0, R1, lane, 0xffffffffu);
+        const double *R = hermite_r<32>(ct, L, q.X, q.Y, q.Z, F, R0, R1, lane, 0xffffffffu);
         double pm = 0.0;
         for (int r = 0; r < 4; ++r) {
           const int kc = lane + 32 * r;
@@ -525,6 +468,22 @@ static cudaError_t configure_g(Tier &t) {
 }
 
 cudaError_t configure_tier(Tier &t) {
+  if (t.reg_cb >= 0) {
+    t.warps_per_block = 4;
+    t.smem = 0;
+    int per_sm = 0;
+    cudaError_t e = occupancy_reg_a(t.reg_cb, t.reg_ck, 128, &per_sm);
+    if (e == cudaErrorInvalidValue) e = occupancy_reg_b(t.reg_cb, t.reg_ck, 128, &per_sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1) per_sm = 1;
+    t.blocks = nsm * per_sm;
+    const int need = (t.nunits + 3) / 4;
+    if (t.blocks > need) t.blocks = need > 0 ? need : 1;
+    return cudaSuccess;
+  }
   switch (t.G) {
     case 1: return configure_g<1>(t);
     case 2: return configure_g<2>(t);
@@ -539,6 +498,26 @@ cudaError_t configure_tier(Tier &t) {
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh, double tau,
                            double *J, double *K, int *counter, cudaStream_t st) {
   if (t.nunits == 0) return cudaSuccess;
+  if (t.reg_cb >= 0) {
+    KArgs a;
+    a.dp = dp;
+    a.nprimtot = dp.nprim_total;
+    a.nEtot = dp.nE_total;
+    a.D = D;
+    a.Dsh = Dsh;
+    a.tau = tau;
+    a.J = J;
+    a.K = K;
+    a.units = t.d_units;
+    a.nunits = t.nunits;
+    a.counter = counter;
+    a.stride = 0;
+    a.boys = dev_boys();
+    a.tabs = dev_class_tables();
+    cudaError_t e = launch_reg_a(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
+    if (e == cudaErrorInvalidValue) e = launch_reg_b(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
+    return e;
+  }
   // The dynamic shared-memory limit is a per-function attribute shared by
   // every handle; raise it to this tier's need before launching.
   cudaError_t ae = cudaSuccess;

@@ -1,0 +1,235 @@
+// Per-class register kernels: one thread owns one contracted shell quartet
+// of a fixed angular-momentum class (la lb|lc ld) with total L <= 3; every
+// loop has a compile-time trip count and every intermediate (Boys seeds,
+// Hermite integrals R, half-transformed Y, contracted ERIs) is a register.
+// Same McMurchie-Davidson steps and digestion as the group kernel in
+// kernels_jk.cu (Sec. 4.1 Eqs. MD def, EabP def1-3; Sec. 3.2 digestion).
+#pragma once
+
+#include <type_traits>
+#include <utility>
+
+#include "device_common.cuh"
+#include "kargs.cuh"
+
+namespace fk {
+
+struct TUV {
+  int t, u, v;
+};
+
+__host__ __device__ constexpr int ct_hidx(int t, int u, int v) {
+  return (t + u + v) * (t + u + v + 1) * (t + u + v + 2) / 6 + (u + v) * (u + v + 1) / 2 + v;
+}
+
+// inverse of ct_hidx
+__host__ __device__ constexpr TUV ct_hvec(int e) {
+  int d = 0;
+  while (nherm(d) <= e) ++d;
+  int r = e - (d > 0 ? nherm(d - 1) : 0);
+  int k = 0;
+  while (r > k) {
+    r -= k + 1;
+    ++k;
+  }
+  return TUV{d - k, k - r, r};
+}
+
+// Cartesian component i of a shell of angular momentum l (x^l first).
+__host__ __device__ constexpr TUV ct_cart(int l, int i) {
+  int k = 0;
+  while (i > k) {
+    i -= k + 1;
+    ++k;
+  }
+  return TUV{l - k, k - i, i};
+}
+
+__host__ __device__ constexpr int ct_box(int la, int ia, int lb, int ib) {
+  return (ct_cart(la, ia).t + ct_cart(lb, ib).t + 1) * (ct_cart(la, ia).u + ct_cart(lb, ib).u + 1) *
+         (ct_cart(la, ia).v + ct_cart(lb, ib).v + 1);
+}
+
+// offset of Cartesian pair k = ia*ncart(lb)+ib in a primitive pair's E block
+__host__ __device__ constexpr int ct_eoff(int la, int lb, int k) {
+  int o = 0;
+  for (int j = 0; j < k; ++j) o += ct_box(la, j / ncart(lb), lb, j % ncart(lb));
+  return o;
+}
+
+// Compile-time loop: f(std::integral_constant<int, i>) for i = 0..N-1, so
+// that every index derived from i is a constant expression.
+template <class F, int... Is>
+__device__ __forceinline__ void sfor_impl(F &&f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void sfor(F &&f) {
+  sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+#define FK_CI(x) decltype(x)::value
+
+// R^{(0)}_{tuv}, t+u+v <= L, from the seeds F[n] = pref (-2 alpha)^n F_n(T)
+// by R^{(n)}_{t,u,v} = (t-1) R^{(n+1)}_{t-2,u,v} + X_PQ R^{(n+1)}_{t-1,u,v}
+// (or the same along y, z for t = 0).
+template <int L>
+__device__ __forceinline__ void hermite_r_reg(const double (&F)[L + 1], double X, double Y, double Z,
+                                              double (&R)[nherm(L)]) {
+  double W[L + 1][nherm(L)];
+  W[L][0] = F[L];
+  sfor<L>([&](auto li) {
+    constexpr int n = L - 1 - FK_CI(li);
+    W[n][0] = F[n];
+    sfor<nherm(L - n) - 1>([&](auto ei) {
+      constexpr int e = FK_CI(ei) + 1;
+      constexpr TUV h = ct_hvec(e);
+      if constexpr (h.t > 0) {
+        double v = X * W[n + 1][ct_hidx(h.t - 1, h.u, h.v)];
+        if constexpr (h.t > 1) v = fma((double)(h.t - 1), W[n + 1][ct_hidx(h.t - 2, h.u, h.v)], v);
+        W[n][e] = v;
+      } else if constexpr (h.u > 0) {
+        double v = Y * W[n + 1][ct_hidx(h.t, h.u - 1, h.v)];
+        if constexpr (h.u > 1) v = fma((double)(h.u - 1), W[n + 1][ct_hidx(h.t, h.u - 2, h.v)], v);
+        W[n][e] = v;
+      } else {
+        double v = Z * W[n + 1][ct_hidx(h.t, h.u, h.v - 1)];
+        if constexpr (h.v > 1) v = fma((double)(h.v - 1), W[n + 1][ct_hidx(h.t, h.u, h.v - 2)], v);
+        W[n][e] = v;
+      }
+    });
+  });
+  sfor<nherm(L)>([&](auto ei) { R[FK_CI(ei)] = W[0][FK_CI(ei)]; });
+}
+
+template <int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q) {
+  constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+  constexpr int NAB = NA * NB, NCD = NC * ND;
+  constexpr int LAB = LA + LB, L = LA + LB + LC + LD;
+  constexpr int NHAB = nherm(LAB), NHL = nherm(L);
+  const DevPairs &dp = a.dp;
+  const int2 ab = dp.ab[P], cd = dp.ab[Q];
+  const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
+  if (screened(a, sA, sB, sC, sD, P, Q)) return;
+
+  double eri[NAB * NCD];
+  sfor<NAB * NCD>([&](auto i) { eri[FK_CI(i)] = 0.0; });
+  const int2 pb = dp.prim[P], pk = dp.prim[Q];
+  for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
+    const PZ P4 = dp.pz[ip];
+    const float4 Pf = dp.pf[ip];
+    const double UsP = dp.U[ip];
+    double Y[NHAB * NCD];
+    sfor<NHAB * NCD>([&](auto i) { Y[FK_CI(i)] = 0.0; });
+    for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
+      const PrimQuartet q = prim_quartet(P4, Pf, UsP, dp.pz[jq], dp.pf[jq], dp.U[jq]);
+      double F[L + 1];
+      boys_seeds<L>(a.boys, q, F);
+      double R[NHL];
+      hermite_r_reg<L>(F, q.X, q.Y, q.Z, R);
+      // ket transform: Y[p][cd] += sum_q (-1)^{|q|} E^{cd}_q R_{p+q}
+      const double *__restrict__ EQ = dp.E + dp.eoff[jq];
+      sfor<NCD>([&](auto kci) {
+        constexpr int kc = FK_CI(kci);
+        constexpr TUV c = ct_cart(LC, kc / ND), d = ct_cart(LD, kc % ND);
+        constexpr int TY = c.u + d.u + 1, TZ = c.v + d.v + 1, NQ = (c.t + d.t + 1) * TY * TZ;
+        constexpr int e0 = ct_eoff(LC, LD, kc);
+        sfor<NQ>([&](auto qi) {
+          constexpr int qq = FK_CI(qi);
+          constexpr int t = qq / (TY * TZ), u = (qq / TZ) % TY, v = qq % TZ;
+          const double e1 = __ldg(EQ + e0 + qq);
+          const double ev = ((t + u + v) & 1) ? -e1 : e1;
+          sfor<NHAB>([&](auto pi) {
+            constexpr int p = FK_CI(pi);
+            constexpr TUV h = ct_hvec(p);
+            Y[p * NCD + kc] = fma(ev, R[ct_hidx(h.t + t, h.u + u, h.v + v)], Y[p * NCD + kc]);
+          });
+        });
+      });
+    }
+    // bra transform: ERI[ab][cd] += sum_p E^{ab}_p Y[p][cd]
+    const double *__restrict__ EP = dp.E + dp.eoff[ip];
+    sfor<NAB>([&](auto kai) {
+      constexpr int ka = FK_CI(kai);
+      constexpr TUV c = ct_cart(LA, ka / NB), d = ct_cart(LB, ka % NB);
+      constexpr int TY = c.u + d.u + 1, TZ = c.v + d.v + 1, NQ = (c.t + d.t + 1) * TY * TZ;
+      constexpr int e0 = ct_eoff(LA, LB, ka);
+      sfor<NQ>([&](auto qi) {
+        constexpr int qq = FK_CI(qi);
+        constexpr int t = qq / (TY * TZ), u = (qq / TZ) % TY, v = qq % TZ;
+        const double ev = __ldg(EP + e0 + qq);
+        sfor<NCD>([&](auto kci) {
+          constexpr int kc = FK_CI(kci);
+          eri[ka * NCD + kc] = fma(ev, Y[ct_hidx(t, u, v) * NCD + kc], eri[ka * NCD + kc]);
+        });
+      });
+    });
+  }
+
+  // digestion into the six J/K blocks (8-fold symmetry, Sec. 2.3 / 3.2)
+  double fac = 1.0;
+  if (sA == sB) fac *= 0.5;
+  if (sC == sD) fac *= 0.5;
+  if (P == Q) fac *= 0.5;
+  const double fac2 = 2.0 * fac;
+  const int N = dp.nbf;
+  const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
+  const double *__restrict__ Dm = a.D;
+  auto E4 = [&](int ia, int ib, int ic, int id) -> double { return eri[(ia * NB + ib) * NCD + ic * ND + id]; };
+  auto Dv = [&](int r, int c) -> double { return __ldg(Dm + (size_t)r * N + c); };
+  sfor<NAB>([&](auto k) {  // J_ab += (ab|cd) D_cd
+    constexpr int ia = FK_CI(k) / NB, ib = FK_CI(k) % NB;
+    double s = 0.0;
+    sfor<NCD>([&](auto m) { s = fma(E4(ia, ib, FK_CI(m) / ND, FK_CI(m) % ND), Dv(fc + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
+    atomicAdd(a.J + (size_t)(fa + ia) * N + fb + ib, fac2 * s);
+  });
+  sfor<NCD>([&](auto k) {  // J_cd += (ab|cd) D_ab
+    constexpr int ic = FK_CI(k) / ND, id = FK_CI(k) % ND;
+    double s = 0.0;
+    sfor<NAB>([&](auto m) { s = fma(E4(FK_CI(m) / NB, FK_CI(m) % NB, ic, id), Dv(fa + FK_CI(m) / NB, fb + FK_CI(m) % NB), s); });
+    atomicAdd(a.J + (size_t)(fc + ic) * N + fd + id, fac2 * s);
+  });
+  sfor<NA * NC>([&](auto k) {  // K_ac += (ab|cd) D_bd
+    constexpr int ia = FK_CI(k) / NC, ic = FK_CI(k) % NC;
+    double s = 0.0;
+    sfor<NB * ND>([&](auto m) { s = fma(E4(ia, FK_CI(m) / ND, ic, FK_CI(m) % ND), Dv(fb + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
+    atomicAdd(a.K + (size_t)(fa + ia) * N + fc + ic, fac * s);
+  });
+  sfor<NA * ND>([&](auto k) {  // K_ad += (ab|cd) D_bc
+    constexpr int ia = FK_CI(k) / ND, id = FK_CI(k) % ND;
+    double s = 0.0;
+    sfor<NB * NC>([&](auto m) { s = fma(E4(ia, FK_CI(m) / NC, FK_CI(m) % NC, id), Dv(fb + FK_CI(m) / NC, fc + FK_CI(m) % NC), s); });
+    atomicAdd(a.K + (size_t)(fa + ia) * N + fd + id, fac * s);
+  });
+  sfor<NB * NC>([&](auto k) {  // K_bc += (ab|cd) D_ad
+    constexpr int ib = FK_CI(k) / NC, ic = FK_CI(k) % NC;
+    double s = 0.0;
+    sfor<NA * ND>([&](auto m) { s = fma(E4(FK_CI(m) / ND, ib, ic, FK_CI(m) % ND), Dv(fa + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
+    atomicAdd(a.K + (size_t)(fb + ib) * N + fc + ic, fac * s);
+  });
+  sfor<NB * ND>([&](auto k) {  // K_bd += (ab|cd) D_ac
+    constexpr int ib = FK_CI(k) / ND, id = FK_CI(k) % ND;
+    double s = 0.0;
+    sfor<NA * NC>([&](auto m) { s = fma(E4(FK_CI(m) / NC, ib, FK_CI(m) % NC, id), Dv(fa + FK_CI(m) / NC, fc + FK_CI(m) % NC), s); });
+    atomicAdd(a.K + (size_t)(fb + ib) * N + fd + id, fac * s);
+  });
+}
+
+template <int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(128) k_reg(KArgs a) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    const int u = next_unit(a.counter, lane);
+    if (u >= a.nunits) break;
+    const Unit un = a.units[u];
+    for (int Q = un.k0 + lane; Q < un.k1; Q += 32) quartet_reg<LA, LB, LC, LD>(a, un.bra, Q);
+  }
+}
+
+// (bra class, ket class) pairs served by register kernels: total L <= 3
+__host__ __device__ constexpr bool reg_class_pair(int cb, int ck) {
+  constexpr int Lc[NCLASS] = {0, 1, 2, 2, 3, 4, 3, 4, 5, 6};
+  return cb >= 0 && ck >= 0 && cb < NCLASS && ck < NCLASS && Lc[cb] + Lc[ck] <= 3;
+}
+
+}  // namespace fk
