@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--carbons", type=int, default=20, help="alkane length for --config 1 (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--warp-scratch", type=int, default=0, help="shared-memory doubles per warp (0 = library default)")
+    ap.add_argument("--reg-max-l", type=int, default=0, help="largest total L served by register kernels (0 = default)")
     return ap.parse_args()
 
 
@@ -203,7 +205,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     p = molgen.problem(args.config, carbons=args.carbons)
-    builder = fk.JKBuilder(p.basis, p.tau)
+    builder = fk.JKBuilder(p.basis, p.tau, fk.make_opts(warp_scratch=args.warp_scratch, reg_max_L=args.reg_max_l))
     st = builder.stats(p.D)
     nk = fk.fock_kernels_per_build(builder.handle)
     D = torch.tensor(p.D, device=dev, dtype=torch.float64)

@@ -81,7 +81,13 @@ typedef struct {
                            tau * prune_eps (default 1e-3; 0 disables)           */
   int32_t group_override; /* 0 = autotuned per class pair; 1..32 = lanes per
                              quartet forced for every class pair (testing)     */
-  int32_t reserved[7];
+  int32_t warp_scratch;   /* shared-memory doubles one warp may use for the
+                             intermediates of its quartets (0 = default 1536);
+                             sets lanes per quartet against occupancy          */
+  int32_t reg_max_L;      /* class pairs with total angular momentum up to this
+                             use the per-class register kernels (0 = default 4;
+                             -1 = none)                                          */
+  int32_t reserved[5];
 } fock_opts;
 
 typedef struct fock_shellpairs fock_shellpairs; /* opaque, library-owned */

@@ -293,7 +293,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
   o.group_override = 0;
   if (opts) o = *opts;
   if (o.precision != FOCK_FP64 && o.precision != FOCK_MIXED) return FOCK_ERR_INVALID_ARG;
-  if (!(o.prune_eps >= 0.0) || o.group_override < 0 || o.group_override > 32 ||
+  if (!(o.prune_eps >= 0.0) || o.group_override < 0 || o.group_override > 32 || o.warp_scratch < 0 ||
       (o.group_override & (o.group_override - 1)) != 0)
     return FOCK_ERR_INVALID_ARG;
 
@@ -474,14 +474,19 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
       class_l(bins[t.bra].cls, la, lb);
       class_l(bins[t.ket].cls, lc, ld);
       t.scratch = scratch_doubles(la, lb, lc, ld);
+      const int budget = o.warp_scratch > 0 ? o.warp_scratch : 1536;
       int G = 1;
-      while (G < 32 && (32 / G) * t.scratch > 3072) G *= 2;
+      while (G < 32 && (32 / G) * t.scratch > budget) G *= 2;
       if (o.group_override > 0) {  // forced group size, raised where one warp's scratch would not fit
         G = o.group_override;
         while (G < 32 && (32 / G) * t.scratch > 24000) G *= 2;
       }
       t.G = G;
-      t.reg = o.group_override == 0 && reg_class_pair(bins[t.bra].cls, bins[t.ket].cls);
+      {
+        const int reg_max = o.reg_max_L == 0 ? 4 : o.reg_max_L;
+        const int Ltot = lxa + lxb + lya + lyb;
+        t.reg = o.group_override == 0 && Ltot <= reg_max && reg_class_pair(bins[t.bra].cls, bins[t.ket].cls);
+      }
       tasks.push_back(t);
     }
   std::stable_sort(tasks.begin(), tasks.end(), [](const Task &a, const Task &b) { return a.cost > b.cost; });

@@ -474,6 +474,7 @@ cudaError_t configure_tier(Tier &t) {
     int per_sm = 0;
     cudaError_t e = occupancy_reg_a(t.reg_cb, t.reg_ck, 128, &per_sm);
     if (e == cudaErrorInvalidValue) e = occupancy_reg_b(t.reg_cb, t.reg_ck, 128, &per_sm);
+    if (e == cudaErrorInvalidValue) e = occupancy_reg_c(t.reg_cb, t.reg_ck, 128, &per_sm);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -516,6 +517,7 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
     a.tabs = dev_class_tables();
     cudaError_t e = launch_reg_a(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
     if (e == cudaErrorInvalidValue) e = launch_reg_b(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
+    if (e == cudaErrorInvalidValue) e = launch_reg_c(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
     return e;
   }
   // The dynamic shared-memory limit is a per-function attribute shared by

@@ -226,10 +226,10 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
   }
 }
 
-// (bra class, ket class) pairs served by register kernels: total L <= 3
+// (bra class, ket class) pairs served by register kernels: total L <= 4
 __host__ __device__ constexpr bool reg_class_pair(int cb, int ck) {
   constexpr int Lc[NCLASS] = {0, 1, 2, 2, 3, 4, 3, 4, 5, 6};
-  return cb >= 0 && ck >= 0 && cb < NCLASS && ck < NCLASS && Lc[cb] + Lc[ck] <= 3;
+  return cb >= 0 && ck >= 0 && cb < NCLASS && ck < NCLASS && Lc[cb] + Lc[ck] <= 4;
 }
 
 }  // namespace fk

@@ -36,7 +36,8 @@ class fock_basis_desc(ctypes.Structure):
 
 class fock_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("fp32_cutoff", ctypes.c_double), ("prune_eps", ctypes.c_double),
-                ("group_override", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("group_override", ctypes.c_int32), ("warp_scratch", ctypes.c_int32), ("reg_max_L", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _lock = threading.Lock()
@@ -141,8 +142,11 @@ class _BasisArrays:
                                     None if self.atom is None else _np_ptr(self.atom))
 
 
-def make_opts(precision=FOCK_FP64, fp32_cutoff=1e-5, prune_eps=1e-3, group_override=0) -> fock_opts:
+def make_opts(precision=FOCK_FP64, fp32_cutoff=1e-5, prune_eps=1e-3, group_override=0, warp_scratch=0,
+              reg_max_L=0) -> fock_opts:
     o = fock_opts()
+    o.reg_max_L = reg_max_L
+    o.warp_scratch = warp_scratch
     o.precision = precision
     o.fp32_cutoff = fp32_cutoff
     o.prune_eps = prune_eps
