@@ -101,19 +101,39 @@ __device__ __forceinline__ void hermite_r_reg(const double (&F)[L + 1], double X
   sfor<nherm(L)>([&](auto ei) { R[FK_CI(ei)] = W[0][FK_CI(ei)]; });
 }
 
+// Classes whose contracted-ERI accumulator and half-transformed Y together
+// would overflow the register file keep the accumulator in shared memory
+// (one column per thread, [element][thread] layout, no bank conflicts).
 template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q) {
+__host__ __device__ constexpr bool reg_eri_in_smem() {
+  return ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD) + nherm(LA + LB) * ncart(LC) * ncart(LD) > 140;
+}
+template <int LA, int LB, int LC, int LD>
+__host__ __device__ constexpr int reg_smem_bytes(int threads) {
+  return reg_eri_in_smem<LA, LB, LC, LD>() ? ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD) * threads * 8 : 0;
+}
+
+template <int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q, double *eri_col) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
   constexpr int NAB = NA * NB, NCD = NC * ND;
   constexpr int LAB = LA + LB, L = LA + LB + LC + LD;
   constexpr int NHAB = nherm(LAB), NHL = nherm(L);
+  constexpr bool SM = reg_eri_in_smem<LA, LB, LC, LD>();
   const DevPairs &dp = a.dp;
   const int2 ab = dp.ab[P], cd = dp.ab[Q];
   const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
   if (screened(a, sA, sB, sC, sD, P, Q)) return;
 
-  double eri[NAB * NCD];
-  sfor<NAB * NCD>([&](auto i) { eri[FK_CI(i)] = 0.0; });
+  double eri_r[SM ? 1 : NAB * NCD];
+  const int bs = blockDim.x;
+  auto eri_at = [&](int i) -> double & {
+    if constexpr (SM)
+      return eri_col[i * bs];
+    else
+      return eri_r[i];
+  };
+  sfor<NAB * NCD>([&](auto i) { eri_at(FK_CI(i)) = 0.0; });
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
     const PZ P4 = dp.pz[ip];
@@ -160,7 +180,7 @@ __device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q) {
         const double ev = __ldg(EP + e0 + qq);
         sfor<NCD>([&](auto kci) {
           constexpr int kc = FK_CI(kci);
-          eri[ka * NCD + kc] = fma(ev, Y[ct_hidx(t, u, v) * NCD + kc], eri[ka * NCD + kc]);
+          eri_at(ka * NCD + kc) = fma(ev, Y[ct_hidx(t, u, v) * NCD + kc], eri_at(ka * NCD + kc));
         });
       });
     });
@@ -175,7 +195,7 @@ __device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q) {
   const int N = dp.nbf;
   const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
   const double *__restrict__ Dm = a.D;
-  auto E4 = [&](int ia, int ib, int ic, int id) -> double { return eri[(ia * NB + ib) * NCD + ic * ND + id]; };
+  auto E4 = [&](int ia, int ib, int ic, int id) -> double { return eri_at((ia * NB + ib) * NCD + ic * ND + id); };
   auto Dv = [&](int r, int c) -> double { return __ldg(Dm + (size_t)r * N + c); };
   sfor<NAB>([&](auto k) {  // J_ab += (ab|cd) D_cd
     constexpr int ia = FK_CI(k) / NB, ib = FK_CI(k) % NB;
@@ -217,12 +237,14 @@ __device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q) {
 
 template <int LA, int LB, int LC, int LD>
 __global__ void __launch_bounds__(128) k_reg(KArgs a) {
+  extern __shared__ __align__(16) double reg_smem[];
   const int lane = threadIdx.x & 31;
+  double *eri_col = reg_smem + threadIdx.x;
   for (;;) {
     const int u = next_unit(a.counter, lane);
     if (u >= a.nunits) break;
     const Unit un = a.units[u];
-    for (int Q = un.k0 + lane; Q < un.k1; Q += 32) quartet_reg<LA, LB, LC, LD>(a, un.bra, Q);
+    for (int Q = un.k0 + lane; Q < un.k1; Q += 32) quartet_reg<LA, LB, LC, LD>(a, un.bra, Q, eri_col);
   }
 }
 
