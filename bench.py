@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warp-scratch", type=int, default=0, help="shared-memory doubles per warp (0 = library default)")
     ap.add_argument("--reg-max-l", type=int, default=0, help="largest total L served by register kernels (0 = default)")
+    ap.add_argument("--fp32-cutoff", type=float, default=1e-5, help="mixed leg: FP32 below this quartet bound")
+    ap.add_argument("--no-mixed-leg", action="store_true")
     return ap.parse_args()
 
 
@@ -267,8 +269,37 @@ def main():
     e2e_value = world * st["eris_schwarz"] * args.steps / (e2e_ms * 1e-3)
     assert np.isfinite(Jh.numpy()).all() and np.isfinite(Kh.numpy()).all()
 
+    # ---- mixed-precision leg on the same workload (extra key) --------------
+    mixed = None
+    if not args.no_mixed_leg:
+        mb = fk.JKBuilder(p.basis, p.tau, fk.make_opts(precision=fk.FOCK_MIXED, fp32_cutoff=args.fp32_cutoff,
+                                                      warp_scratch=args.warp_scratch, reg_max_L=args.reg_max_l))
+        mst = mb.stats(p.D)
+        builder.build(D, J, K)
+        Jm = torch.empty_like(D)
+        Km = torch.empty_like(D)
+        for _ in range(max(3, args.warmup)):
+            mb.build(D, Jm, Km)
+        torch.cuda.synchronize(dev)
+        mevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for s, e in mevs:
+            flush.zero_()
+            s.record(stream)
+            mb.build(D, Jm, Km)
+            e.record(stream)
+        torch.cuda.synchronize(dev)
+        mms = float(sum(s.elapsed_time(e) for s, e in mevs)) / args.steps
+        err = max(float((Jm - J).abs().max()), float((Km - K).abs().max()))
+        trd = abs(float((D * (2 * Jm - Km)).sum() - (D * (2 * J - K)).sum()))
+        mixed = {"ms_per_step": mms, "value": st["eris_schwarz"] / (mms * 1e-3), "unit": UNIT,
+                 "speedup_vs_fp64": ms / mms, "fp32_cutoff": args.fp32_cutoff,
+                 "max_abs_diff_vs_fp64": err, "trace_diff_vs_fp64": trd,
+                 "fp32_quartet_share": mst["quartets_fp32"] / max(1.0, mst["quartets_evaluated"]),
+                 "fp32_flop_share": mst["flops_model_fp32"] / max(1.0, mst["flops_model"])}
+        mb.close()
+
     if rank == 0:
-        achieved = st["fp64_flops_model"] / (ms * 1e-3) / 1e12
+        achieved = st["flops_model"] / (ms * 1e-3) / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "s_per_iteration": ms * 1e-3,
@@ -281,9 +312,10 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(D.numel() * 8),
                     "d2h_bytes_per_step": int(2 * D.numel() * 8)},
             "gpu_launches": int(nk * args.steps),
+            "mixed": mixed,
             "clocks": clk.summary(),
             "work": {k: st[k] for k in ("quartets_evaluated", "eris_evaluated", "prim_quartets",
-                                        "fp64_flops_model", "prim_pairs", "pairs")},
+                                        "flops_model", "prim_pairs", "pairs")},
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p)

@@ -187,10 +187,12 @@ FOCK_API fock_status fock_build_jk_batched(const fock_shellpairs *const *bases, 
  *          Hermite transforms, digestion)
  *   out[6] primitive pairs kept after pruning
  *   out[7] contracted pairs kept
+ *   out[8] evaluated quartets taken by the FP32 path (mixed precision)
+ *   out[9] modelled floating-point operations of those FP32 quartets
  * D: host, N x N row-major float64.  Synchronous.
  */
 FOCK_API fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host,
-                            double schwarz_thresh, double out[8]);
+                            double schwarz_thresh, double out[10]);
 
 /* Number of kernels one fock_build_jk call on this handle launches (density
  * preparation, one persistent ERI/digestion kernel per work tier, the final

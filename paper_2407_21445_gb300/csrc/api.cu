@@ -31,6 +31,8 @@ struct Staging {  // host arrays mirroring DevPairs
   std::vector<double> U;
   std::vector<int> eoff;
   std::vector<double> E;
+  std::vector<float4> paf;
+  std::vector<float> Uf, Ef;
 };
 
 // Device copy of a Staging set plus units: one allocation, 256-byte aligned
@@ -172,6 +174,9 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   const size_t o_U = pk.add(st.U.data(), st.U.size() * sizeof(double));
   const size_t o_eoff = pk.add(st.eoff.data(), st.eoff.size() * sizeof(int));
   const size_t o_E = pk.add(st.E.data(), st.E.size() * sizeof(double));
+  const size_t o_paf = pk.add(st.paf.data(), st.paf.size() * sizeof(float4));
+  const size_t o_Uf = pk.add(st.Uf.data(), st.Uf.size() * sizeof(float));
+  const size_t o_Ef = pk.add(st.Ef.data(), st.Ef.size() * sizeof(float));
   const size_t o_units = pk.add(units.data(), units.size() * sizeof(Unit));
   const size_t total = (pk.off + 255) & ~(size_t)255;
   char *d = nullptr;
@@ -197,6 +202,9 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   dp.U = (const double *)(d + o_U);
   dp.eoff = (const int *)(d + o_eoff);
   dp.E = (const double *)(d + o_E);
+  dp.paf = (const float4 *)(d + o_paf);
+  dp.Uf = (const float *)(d + o_Uf);
+  dp.Ef = (const float *)(d + o_Ef);
   dp.npair = (int)st.ab.size();
   dp.nprim_total = (int)st.pz.size();
   dp.nE_total = (long long)st.E.size();
@@ -344,6 +352,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
           const PZ pz{(al * A[0] + be * B[0]) / p, (al * A[1] + be * B[1]) / p, (al * A[2] + be * B[2]) / p, p};
           all.pz.push_back(pz);
           all.pf.push_back(make_float4((float)pz.x, (float)pz.y, (float)pz.z, (float)p));
+          all.paf.push_back(make_float4((float)(pz.x - A[0]), (float)(pz.y - A[1]), (float)(pz.z - A[2]), (float)p));
           // U_P sqrt(zeta) (2/sqrt(pi))^(1/2), so that U_P U_Q 2 sqrt(alpha/pi) = Us_P Us_Q / sqrt(zeta + eta)
           all.U.push_back(cn[a][i] * cn[b][j] * pow(kPi / p, 1.5) * exp(-al * be / p * AB2) * sqrt(p) *
                           sqrt(2.0 / sqrt(kPi)));
@@ -423,10 +432,13 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     for (int i : kept_prims[P]) {
       st.pz.push_back(all.pz[i]);
       st.pf.push_back(all.pf[i]);
+      st.paf.push_back(all.paf[i]);
       st.U.push_back(all.U[i]);
+      st.Uf.push_back((float)all.U[i]);
       st.eoff.push_back((int)st.E.size());
       const int n = ct.nE[all.cls[P]];
       st.E.insert(st.E.end(), all.E.begin() + all.eoff[i], all.E.begin() + all.eoff[i] + n);
+      for (int k = 0; k < n; ++k) st.Ef.push_back((float)all.E[all.eoff[i] + k]);
     }
   }
 
@@ -593,13 +605,17 @@ fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double sch
   if (!(schwarz_thresh >= sp->tau_build) || !isfinite(schwarz_thresh)) return FOCK_ERR_INVALID_ARG;
   const int ns = sp->nshell, n = sp->nbf;
   const size_t nt = sp->tiers.size();
+  const bool mixed = sp->opts.precision == FOCK_MIXED && sp->opts.fp32_cutoff > 0.0;
   const size_t dsh_bytes = sizeof(double) * (size_t)ns * ns;
   const size_t cnt_off = (dsh_bytes + 255) & ~(size_t)255;
+  const size_t df_off = (cnt_off + sizeof(int) * (nt + 1) + 255) & ~(size_t)255;
+  const size_t total = mixed ? df_off + sizeof(float) * (size_t)n * n : df_off;
   char *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&scratch, cnt_off + sizeof(int) * (nt + 1), stream);
+  cudaError_t e = cudaMallocAsync((void **)&scratch, total, stream);
   if (e != cudaSuccess) return to_status(e);
   double *Dsh = (double *)scratch;
   int *counters = (int *)(scratch + cnt_off);
+  float *Df = mixed ? (float *)(scratch + df_off) : nullptr;
   const bool chk = sync_check();
   const char *where = "memset";
   e = cudaMemsetAsync(counters, 0, sizeof(int) * (nt + 1), stream);
@@ -607,14 +623,15 @@ fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double sch
   if (e == cudaSuccess) e = cudaMemsetAsync(K, 0, sizeof(double) * (size_t)n * n, stream);
   if (e == cudaSuccess) {
     where = "k_dprep";
-    e = launch_dprep(D, n, sp->dev.sbf, sp->dev.sl, ns, Dsh, stream);
+    e = launch_dprep(D, n, sp->dev.sbf, sp->dev.sl, ns, Dsh, stream, Df);
     if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
   }
   static char tier_name[64];
   for (size_t t = 0; t < nt && e == cudaSuccess; ++t) {
     snprintf(tier_name, sizeof(tier_name), "k_jk tier %zu (G=%d, smem=%zu)", t, sp->tiers[t].G, sp->tiers[t].smem);
     where = tier_name;
-    e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, J, K, counters + t, stream);
+    e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, J, K, counters + t, stream, Df,
+                       sp->opts.fp32_cutoff);
     if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
   }
   if (e == cudaSuccess) {
@@ -647,7 +664,7 @@ fock_status fock_stream_status(cudaStream_t stream) {
   return (fock_status)v;
 }
 
-fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, double schwarz_thresh, double out[8]) {
+fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, double schwarz_thresh, double out[10]) {
   if (!sp || !D_host || !out) return FOCK_ERR_INVALID_ARG;
   if (!(schwarz_thresh >= sp->tau_build)) return FOCK_ERR_INVALID_ARG;
   const int ns = sp->nshell, n = sp->nbf;
@@ -660,9 +677,12 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
           mx = std::max(mx, fabs(D_host[(size_t)(sp->h_sbf[a] + i) * n + sp->h_sbf[b] + j]));
       Dsh[(size_t)a * ns + b] = mx;
     }
-  double q1 = 0, e1 = 0, q2 = 0, e2 = 0, pq = 0, fl = 0;
+  double q1 = 0, e1 = 0, q2 = 0, e2 = 0, pq = 0, fl = 0, q32 = 0, fl32 = 0;
   const double tau = schwarz_thresh;
-  for (const Unit &u : sp->h_units) {
+  const bool mixed = sp->opts.precision == FOCK_MIXED && sp->opts.fp32_cutoff > 0.0;
+  for (size_t ui = 0; ui < sp->h_units.size(); ++ui) {
+    const Unit &u = sp->h_units[ui];
+    const bool reg = sp->tiers[sp->h_unit_tier[ui]].reg_cb >= 0;
     const int P = u.bra;
     const int2 ab = sp->h_ab[P];
     for (int Q = u.k0; Q < u.k1; ++Q) {
@@ -685,8 +705,13 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
       const double np = (double)sp->h_prim[P].y * sp->h_prim[Q].y;
       pq += np;
       const FlopTable &ft = flop_table();
-      fl += np * ft.prim[sp->h_cls[P]][sp->h_cls[Q]] + sp->h_prim[P].y * ft.bra[sp->h_cls[P]][sp->h_cls[Q]] +
-            12.0 * ne;
+      const double f = np * ft.prim[sp->h_cls[P]][sp->h_cls[Q]] + sp->h_prim[P].y * ft.bra[sp->h_cls[P]][sp->h_cls[Q]] +
+                       12.0 * ne;
+      fl += f;
+      if (mixed && reg && g * dm < sp->opts.fp32_cutoff) {
+        q32 += 1;
+        fl32 += f;
+      }
     }
   }
   double nprim = 0;
@@ -699,6 +724,8 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
   out[5] = fl;
   out[6] = nprim;
   out[7] = (double)sp->h_ab.size();
+  out[8] = q32;
+  out[9] = fl32;
   return FOCK_OK;
 }
 

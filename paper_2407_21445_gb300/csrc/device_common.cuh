@@ -147,4 +147,47 @@ __device__ __forceinline__ void boys_seeds_rt(const double *__restrict__ tab, co
   }
 }
 
+// Exact float -> double on the integer units for any finite float
+// (zero and subnormal inputs map to 0, |x| < 1.2e-38).
+__device__ __forceinline__ double f2d_any(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long e = ex + (1023u - 127u);
+  const unsigned long long m = u & 0x7fffffu;
+  return __longlong_as_double((long long)(sign | (e << 52) | (m << 29)));
+}
+
+// FP32 seeds pref (-2 alpha)^m F_m(T), m = 0..L: six Taylor terms from the
+// FP32 copy of the table (truncation < 2e-12 relative) or the asymptotic form.
+template <int L>
+__device__ __forceinline__ void boys_seeds_f32(const float *__restrict__ tab, float T, float pref, float m2a,
+                                               float (&out)[L + 1]) {
+  if (T < (float)BOYS_TMAX) {
+    const int gi = __float2int_rn(T * (float)BOYS_INVH);
+    const float x = (float)gi * (float)BOYS_H - T;
+#pragma unroll
+    for (int m = 0; m <= L; ++m) {
+      const float *c = tab + ((size_t)gi * (LTOT + 1) + m) * BOYS_TAYLOR;
+      float f = __ldg(c + 5);
+#pragma unroll
+      for (int k = 4; k >= 0; --k) f = fmaf(f, x, __ldg(c + k));
+      out[m] = f;
+    }
+  } else {
+    const float rt = rsqrtf(T);
+    out[0] = 0.886226925452758f * rt;
+    const float it = rt * rt;
+#pragma unroll
+    for (int m = 1; m <= L; ++m) out[m] = out[m - 1] * ((m - 0.5f) * it);
+  }
+  float c = pref;
+#pragma unroll
+  for (int m = 0; m <= L; ++m) {
+    out[m] *= c;
+    c *= m2a;
+  }
+}
+
 }  // namespace fk

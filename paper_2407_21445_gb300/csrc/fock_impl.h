@@ -82,6 +82,10 @@ struct DevPairs {
   const double *U;     // U_P sqrt(zeta) (2/sqrt(pi))^(1/2): pref = U_P U_Q / sqrt(zeta + eta)
   const int *eoff;     // offset of the primitive pair's E block
   const double *E;     // Hermite coefficients (Cartesian normalisation folded in)
+  // FP32 copies for the mixed-precision path
+  const float4 *paf;   // (P - A, zeta) with A the first shell of the canonical pair
+  const float *Uf;     // U as above, FP32
+  const float *Ef;     // Hermite coefficients, FP32
   int nshell, nbf, npair;
   int nprim_total;
   long long nE_total;
@@ -140,12 +144,14 @@ void hermite_pair(int la, int lb, double alpha, const double *A, double beta, co
 // device entry points (kernels.cu)
 cudaError_t upload_tables(cudaStream_t st);
 const double *dev_boys();
+const float *dev_boys_f();
 const ClassTables *dev_class_tables();
 cudaError_t launch_schwarz(const DevPairs &dp, double *Gpair, double *Gprim, cudaStream_t st);
 cudaError_t launch_dprep(const double *D, int nbf, const int *sbf, const int *sl, int nshell,
-                         double *Dsh, cudaStream_t st);
+                         double *Dsh, cudaStream_t st, float *Df = nullptr);
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh,
-                           double tau, double *J, double *K, int *counter, cudaStream_t st);
+                           double tau, double *J, double *K, int *counter, cudaStream_t st,
+                           const float *Df = nullptr, double fp32_cutoff = 0.0);
 cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st);
 cudaError_t configure_tier(Tier &t);
 int read_and_clear_status(cudaStream_t st, int *status);

@@ -20,7 +20,27 @@ struct KArgs {
   int stride;
   const double *boys;
   const ClassTables *tabs;
+  // mixed precision: quartets with bound below fp32_cutoff use the FP32 path
+  double fp32_cutoff;  // 0 = FP64 only
+  const float *Df;     // FP32 copy of D (mixed path)
+  const float *boysf;  // FP32 Boys table (same layout)
 };
+
+// Density-weighted Schwarz bound G_ab G_cd max|D| over the six blocks
+// (Sec. 3.2); returns a negative value when the quartet is screened out.
+__device__ __forceinline__ double quartet_bound(const KArgs &a, int sA, int sB, int sC, int sD, int P, int Q) {
+  const double g = a.dp.G[P] * a.dp.G[Q];
+  const int ns = a.dp.nshell;
+  const double *Ds = a.Dsh;
+  double dm = Ds[sA * ns + sB];
+  dm = fmax(dm, Ds[sC * ns + sD]);
+  dm = fmax(dm, Ds[sA * ns + sC]);
+  dm = fmax(dm, Ds[sA * ns + sD]);
+  dm = fmax(dm, Ds[sB * ns + sC]);
+  dm = fmax(dm, Ds[sB * ns + sD]);
+  const double b = g * dm;
+  return (g < a.tau || b < a.tau) ? -1.0 : b;
+}
 
 // Density-weighted Schwarz test of quartet (P|Q) (Sec. 3.2): true = skip.
 __device__ __forceinline__ bool screened(const KArgs &a, int sA, int sB, int sC, int sD, int P, int Q) {

@@ -53,6 +53,7 @@ __device__ long long g_bounds[2] = {0, 0};
 #endif
 
 static double *s_boys[64];
+static float *s_boysf[64];
 static ClassTables *s_tabs[64];
 
 
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(128) k_schwarz(DevPairs dp, const double *boys
 
 // Shell-block maxima |D| (Sec. 3.2 density screening) and a finiteness check.
 __global__ void k_dprep(const double *__restrict__ D, int N, const int *__restrict__ sbf,
-                        const int *__restrict__ sl, int ns, double *__restrict__ Dsh) {
+                        const int *__restrict__ sl, int ns, double *__restrict__ Dsh, float *__restrict__ Df) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= ns * ns) return;
   const int a = idx / ns, b = idx - a * ns;
@@ -356,6 +357,7 @@ __global__ void k_dprep(const double *__restrict__ D, int N, const int *__restri
   for (int i = 0; i < na; ++i)
     for (int j = 0; j < nb; ++j) {
       const double v = D[(size_t)(fa + i) * N + fb + j];
+      if (Df) Df[(size_t)(fa + i) * N + fb + j] = (float)v;
       if (!isfinite(v)) bad = true;
       mx = fmax(mx, fabs(v));
     }
@@ -387,24 +389,34 @@ cudaError_t upload_tables(cudaStream_t st) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (s_boys[dev] && s_tabs[dev]) return cudaSuccess;
+  if (s_boys[dev] && s_tabs[dev] && s_boysf[dev]) return cudaSuccess;
   const std::vector<double> &bt = boys_table();
+  std::vector<float> btf(bt.begin(), bt.end());
   double *b = nullptr;
+  float *bf = nullptr;
   ClassTables *t = nullptr;
   if ((e = cudaMalloc(&b, bt.size() * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&t, sizeof(ClassTables))) != cudaSuccess) {
+  if ((e = cudaMalloc(&bf, btf.size() * sizeof(float))) != cudaSuccess) {
     cudaFree(b);
     return e;
   }
+  if ((e = cudaMalloc(&t, sizeof(ClassTables))) != cudaSuccess) {
+    cudaFree(b);
+    cudaFree(bf);
+    return e;
+  }
   e = cudaMemcpyAsync(b, bt.data(), bt.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bf, btf.data(), btf.size() * sizeof(float), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(t, &class_tables(), sizeof(ClassTables), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaFree(b);
+    cudaFree(bf);
     cudaFree(t);
     return e;
   }
   s_boys[dev] = b;
+  s_boysf[dev] = bf;
   s_tabs[dev] = t;
   return cudaSuccess;
 }
@@ -413,6 +425,11 @@ const double *dev_boys() {
   int dev = 0;
   cudaGetDevice(&dev);
   return s_boys[dev];
+}
+const float *dev_boys_f() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return s_boysf[dev];
 }
 const ClassTables *dev_class_tables() {
   int dev = 0;
@@ -432,9 +449,9 @@ cudaError_t launch_schwarz(const DevPairs &dp, double *Gpair, double *Gprim, cud
 }
 
 cudaError_t launch_dprep(const double *D, int nbf, const int *sbf, const int *sl, int nshell, double *Dsh,
-                         cudaStream_t st) {
+                         cudaStream_t st, float *Df) {
   const int n = nshell * nshell;
-  k_dprep<<<(n + 255) / 256, 256, 0, st>>>(D, nbf, sbf, sl, nshell, Dsh);
+  k_dprep<<<(n + 255) / 256, 256, 0, st>>>(D, nbf, sbf, sl, nshell, Dsh, Df);
   return cudaGetLastError();
 }
 
@@ -475,6 +492,7 @@ cudaError_t configure_tier(Tier &t) {
     cudaError_t e = occupancy_reg_a(t.reg_cb, t.reg_ck, 128, &per_sm);
     if (e == cudaErrorInvalidValue) e = occupancy_reg_b(t.reg_cb, t.reg_ck, 128, &per_sm);
     if (e == cudaErrorInvalidValue) e = occupancy_reg_c(t.reg_cb, t.reg_ck, 128, &per_sm);
+    if (e == cudaErrorInvalidValue) e = occupancy_reg_d(t.reg_cb, t.reg_ck, 128, &per_sm);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -497,7 +515,8 @@ cudaError_t configure_tier(Tier &t) {
 }
 
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh, double tau,
-                           double *J, double *K, int *counter, cudaStream_t st) {
+                           double *J, double *K, int *counter, cudaStream_t st, const float *Df,
+                           double fp32_cutoff) {
   if (t.nunits == 0) return cudaSuccess;
   if (t.reg_cb >= 0) {
     KArgs a;
@@ -515,9 +534,13 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
     a.stride = 0;
     a.boys = dev_boys();
     a.tabs = dev_class_tables();
+    a.fp32_cutoff = Df ? fp32_cutoff : 0.0;
+    a.Df = Df;
+    a.boysf = dev_boys_f();
     cudaError_t e = launch_reg_a(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
     if (e == cudaErrorInvalidValue) e = launch_reg_b(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
     if (e == cudaErrorInvalidValue) e = launch_reg_c(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
+    if (e == cudaErrorInvalidValue) e = launch_reg_d(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
     return e;
   }
   // The dynamic shared-memory limit is a per-function attribute shared by
@@ -548,6 +571,9 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
   a.stride = t.stride;
   a.boys = dev_boys();
   a.tabs = dev_class_tables();
+  a.fp32_cutoff = 0.0;  // the group kernels evaluate every quartet in FP64
+  a.Df = nullptr;
+  a.boysf = dev_boys_f();
   const dim3 blk(32 * t.warps_per_block);
   switch (t.G) {
     case 1: k_jk<1><<<t.blocks, blk, t.smem, st>>>(a); break;

@@ -72,10 +72,9 @@ __device__ __forceinline__ void sfor(F &&f) {
 // R^{(0)}_{tuv}, t+u+v <= L, from the seeds F[n] = pref (-2 alpha)^n F_n(T)
 // by R^{(n)}_{t,u,v} = (t-1) R^{(n+1)}_{t-2,u,v} + X_PQ R^{(n+1)}_{t-1,u,v}
 // (or the same along y, z for t = 0).
-template <int L>
-__device__ __forceinline__ void hermite_r_reg(const double (&F)[L + 1], double X, double Y, double Z,
-                                              double (&R)[nherm(L)]) {
-  double W[L + 1][nherm(L)];
+template <int L, class Real>
+__device__ __forceinline__ void hermite_r_reg(const Real (&F)[L + 1], Real X, Real Y, Real Z, Real (&R)[nherm(L)]) {
+  Real W[L + 1][nherm(L)];
   W[L][0] = F[L];
   sfor<L>([&](auto li) {
     constexpr int n = L - 1 - FK_CI(li);
@@ -84,16 +83,16 @@ __device__ __forceinline__ void hermite_r_reg(const double (&F)[L + 1], double X
       constexpr int e = FK_CI(ei) + 1;
       constexpr TUV h = ct_hvec(e);
       if constexpr (h.t > 0) {
-        double v = X * W[n + 1][ct_hidx(h.t - 1, h.u, h.v)];
-        if constexpr (h.t > 1) v = fma((double)(h.t - 1), W[n + 1][ct_hidx(h.t - 2, h.u, h.v)], v);
+        Real v = X * W[n + 1][ct_hidx(h.t - 1, h.u, h.v)];
+        if constexpr (h.t > 1) v = fma((Real)(h.t - 1), W[n + 1][ct_hidx(h.t - 2, h.u, h.v)], v);
         W[n][e] = v;
       } else if constexpr (h.u > 0) {
-        double v = Y * W[n + 1][ct_hidx(h.t, h.u - 1, h.v)];
-        if constexpr (h.u > 1) v = fma((double)(h.u - 1), W[n + 1][ct_hidx(h.t, h.u - 2, h.v)], v);
+        Real v = Y * W[n + 1][ct_hidx(h.t, h.u - 1, h.v)];
+        if constexpr (h.u > 1) v = fma((Real)(h.u - 1), W[n + 1][ct_hidx(h.t, h.u - 2, h.v)], v);
         W[n][e] = v;
       } else {
-        double v = Z * W[n + 1][ct_hidx(h.t, h.u, h.v - 1)];
-        if constexpr (h.v > 1) v = fma((double)(h.v - 1), W[n + 1][ct_hidx(h.t, h.u, h.v - 2)], v);
+        Real v = Z * W[n + 1][ct_hidx(h.t, h.u, h.v - 1)];
+        if constexpr (h.v > 1) v = fma((Real)(h.v - 1), W[n + 1][ct_hidx(h.t, h.u, h.v - 2)], v);
         W[n][e] = v;
       }
     });
@@ -114,16 +113,14 @@ __host__ __device__ constexpr int reg_smem_bytes(int threads) {
 }
 
 template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q, double *eri_col) {
+__device__ __forceinline__ void quartet_reg_f64(const KArgs &a, int P, int Q, int sA, int sB, int sC, int sD,
+                                                double *eri_col) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
   constexpr int NAB = NA * NB, NCD = NC * ND;
   constexpr int LAB = LA + LB, L = LA + LB + LC + LD;
   constexpr int NHAB = nherm(LAB), NHL = nherm(L);
   constexpr bool SM = reg_eri_in_smem<LA, LB, LC, LD>();
   const DevPairs &dp = a.dp;
-  const int2 ab = dp.ab[P], cd = dp.ab[Q];
-  const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
-  if (screened(a, sA, sB, sC, sD, P, Q)) return;
 
   double eri_r[SM ? 1 : NAB * NCD];
   const int bs = blockDim.x;
@@ -146,7 +143,7 @@ __device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q, double
       double F[L + 1];
       boys_seeds<L>(a.boys, q, F);
       double R[NHL];
-      hermite_r_reg<L>(F, q.X, q.Y, q.Z, R);
+      hermite_r_reg<L, double>(F, q.X, q.Y, q.Z, R);
       // ket transform: Y[p][cd] += sum_q (-1)^{|q|} E^{cd}_q R_{p+q}
       const double *__restrict__ EQ = dp.E + dp.eoff[jq];
       sfor<NCD>([&](auto kci) {
@@ -233,6 +230,137 @@ __device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q, double
     sfor<NA * NC>([&](auto m) { s = fma(E4(FK_CI(m) / NC, ib, FK_CI(m) % NC, id), Dv(fa + FK_CI(m) / NC, fc + FK_CI(m) % NC), s); });
     atomicAdd(a.K + (size_t)(fb + ib) * N + fd + id, fac * s);
   });
+}
+
+// The same quartet in FP32 (mixed-precision path, quartets whose
+// density-weighted bound is below the FP32 cutoff): FP32 Boys table, Hermite
+// recursion, transforms and digestion; centres are taken relative to the
+// pair's first shell so that P - Q keeps its precision; each digested J/K
+// element is converted exactly to FP64 and accumulated in FP64.
+template <int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void quartet_reg_f32(const KArgs &a, int P, int Q, int sA, int sB, int sC, int sD) {
+  constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+  constexpr int NAB = NA * NB, NCD = NC * ND;
+  constexpr int LAB = LA + LB, L = LA + LB + LC + LD;
+  constexpr int NHAB = nherm(LAB), NHL = nherm(L);
+  const DevPairs &dp = a.dp;
+  const float ACx = (float)(dp.sxyz[3 * sA] - dp.sxyz[3 * sC]);
+  const float ACy = (float)(dp.sxyz[3 * sA + 1] - dp.sxyz[3 * sC + 1]);
+  const float ACz = (float)(dp.sxyz[3 * sA + 2] - dp.sxyz[3 * sC + 2]);
+  float eri[NAB * NCD];
+  sfor<NAB * NCD>([&](auto i) { eri[FK_CI(i)] = 0.0f; });
+  const int2 pb = dp.prim[P], pk = dp.prim[Q];
+  for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
+    const float4 PA = dp.paf[ip];
+    const float UP = dp.Uf[ip];
+    float Y[NHAB * NCD];
+    sfor<NHAB * NCD>([&](auto i) { Y[FK_CI(i)] = 0.0f; });
+    for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
+      const float4 QC = dp.paf[jq];
+      const float X = PA.x - QC.x + ACx, Yd = PA.y - QC.y + ACy, Z = PA.z - QC.z + ACz;
+      const float rs = rsqrtf(PA.w + QC.w);
+      const float alpha = (PA.w * QC.w) * (rs * rs);
+      const float T = alpha * fmaf(X, X, fmaf(Yd, Yd, Z * Z));
+      float F[L + 1];
+      boys_seeds_f32<L>(a.boysf, T, UP * dp.Uf[jq] * rs, -2.0f * alpha, F);
+      float R[NHL];
+      hermite_r_reg<L, float>(F, X, Yd, Z, R);
+      const float *__restrict__ EQ = dp.Ef + dp.eoff[jq];
+      sfor<NCD>([&](auto kci) {
+        constexpr int kc = FK_CI(kci);
+        constexpr TUV c = ct_cart(LC, kc / ND), d = ct_cart(LD, kc % ND);
+        constexpr int TY = c.u + d.u + 1, TZ = c.v + d.v + 1, NQ = (c.t + d.t + 1) * TY * TZ;
+        constexpr int e0 = ct_eoff(LC, LD, kc);
+        sfor<NQ>([&](auto qi) {
+          constexpr int qq = FK_CI(qi);
+          constexpr int t = qq / (TY * TZ), u = (qq / TZ) % TY, v = qq % TZ;
+          const float e1 = __ldg(EQ + e0 + qq);
+          const float ev = ((t + u + v) & 1) ? -e1 : e1;
+          sfor<NHAB>([&](auto pi) {
+            constexpr int p = FK_CI(pi);
+            constexpr TUV h = ct_hvec(p);
+            Y[p * NCD + kc] = fmaf(ev, R[ct_hidx(h.t + t, h.u + u, h.v + v)], Y[p * NCD + kc]);
+          });
+        });
+      });
+    }
+    const float *__restrict__ EP = dp.Ef + dp.eoff[ip];
+    sfor<NAB>([&](auto kai) {
+      constexpr int ka = FK_CI(kai);
+      constexpr TUV c = ct_cart(LA, ka / NB), d = ct_cart(LB, ka % NB);
+      constexpr int TY = c.u + d.u + 1, TZ = c.v + d.v + 1, NQ = (c.t + d.t + 1) * TY * TZ;
+      constexpr int e0 = ct_eoff(LA, LB, ka);
+      sfor<NQ>([&](auto qi) {
+        constexpr int qq = FK_CI(qi);
+        constexpr int t = qq / (TY * TZ), u = (qq / TZ) % TY, v = qq % TZ;
+        const float ev = __ldg(EP + e0 + qq);
+        sfor<NCD>([&](auto kci) {
+          constexpr int kc = FK_CI(kci);
+          eri[ka * NCD + kc] = fmaf(ev, Y[ct_hidx(t, u, v) * NCD + kc], eri[ka * NCD + kc]);
+        });
+      });
+    });
+  }
+  float fac = 1.0f;
+  if (sA == sB) fac *= 0.5f;
+  if (sC == sD) fac *= 0.5f;
+  if (P == Q) fac *= 0.5f;
+  const float fac2 = 2.0f * fac;
+  const int N = dp.nbf;
+  const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
+  const float *__restrict__ Dm = a.Df;
+  auto E4 = [&](int ia, int ib, int ic, int id) -> float { return eri[(ia * NB + ib) * NCD + ic * ND + id]; };
+  auto Dv = [&](int r, int c) -> float { return __ldg(Dm + (size_t)r * N + c); };
+  sfor<NAB>([&](auto k) {
+    constexpr int ia = FK_CI(k) / NB, ib = FK_CI(k) % NB;
+    float s = 0.0f;
+    sfor<NCD>([&](auto m) { s = fmaf(E4(ia, ib, FK_CI(m) / ND, FK_CI(m) % ND), Dv(fc + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
+    atomicAdd(a.J + (size_t)(fa + ia) * N + fb + ib, f2d_any(fac2 * s));
+  });
+  sfor<NCD>([&](auto k) {
+    constexpr int ic = FK_CI(k) / ND, id = FK_CI(k) % ND;
+    float s = 0.0f;
+    sfor<NAB>([&](auto m) { s = fmaf(E4(FK_CI(m) / NB, FK_CI(m) % NB, ic, id), Dv(fa + FK_CI(m) / NB, fb + FK_CI(m) % NB), s); });
+    atomicAdd(a.J + (size_t)(fc + ic) * N + fd + id, f2d_any(fac2 * s));
+  });
+  sfor<NA * NC>([&](auto k) {
+    constexpr int ia = FK_CI(k) / NC, ic = FK_CI(k) % NC;
+    float s = 0.0f;
+    sfor<NB * ND>([&](auto m) { s = fmaf(E4(ia, FK_CI(m) / ND, ic, FK_CI(m) % ND), Dv(fb + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
+    atomicAdd(a.K + (size_t)(fa + ia) * N + fc + ic, f2d_any(fac * s));
+  });
+  sfor<NA * ND>([&](auto k) {
+    constexpr int ia = FK_CI(k) / ND, id = FK_CI(k) % ND;
+    float s = 0.0f;
+    sfor<NB * NC>([&](auto m) { s = fmaf(E4(ia, FK_CI(m) / NC, FK_CI(m) % NC, id), Dv(fb + FK_CI(m) / NC, fc + FK_CI(m) % NC), s); });
+    atomicAdd(a.K + (size_t)(fa + ia) * N + fd + id, f2d_any(fac * s));
+  });
+  sfor<NB * NC>([&](auto k) {
+    constexpr int ib = FK_CI(k) / NC, ic = FK_CI(k) % NC;
+    float s = 0.0f;
+    sfor<NA * ND>([&](auto m) { s = fmaf(E4(FK_CI(m) / ND, ib, ic, FK_CI(m) % ND), Dv(fa + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
+    atomicAdd(a.K + (size_t)(fb + ib) * N + fc + ic, f2d_any(fac * s));
+  });
+  sfor<NB * ND>([&](auto k) {
+    constexpr int ib = FK_CI(k) / ND, id = FK_CI(k) % ND;
+    float s = 0.0f;
+    sfor<NA * NC>([&](auto m) { s = fmaf(E4(FK_CI(m) / NC, ib, FK_CI(m) % NC, id), Dv(fa + FK_CI(m) / NC, fc + FK_CI(m) % NC), s); });
+    atomicAdd(a.K + (size_t)(fb + ib) * N + fd + id, f2d_any(fac * s));
+  });
+}
+
+// One quartet: screening, then the FP32 path below the mixed-precision
+// cutoff (0 in the FP64 mode) or the FP64 path.
+template <int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q, double *eri_col) {
+  const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
+  const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
+  const double b = quartet_bound(a, sA, sB, sC, sD, P, Q);
+  if (b < 0.0) return;
+  if (b < a.fp32_cutoff)
+    quartet_reg_f32<LA, LB, LC, LD>(a, P, Q, sA, sB, sC, sD);
+  else
+    quartet_reg_f64<LA, LB, LC, LD>(a, P, Q, sA, sB, sC, sD, eri_col);
 }
 
 template <int LA, int LB, int LC, int LD>

@@ -1,4 +1,4 @@
-// Register-kernel instantiations with total L = 4.
+// Register-kernel instantiations with total L = 4 (s, f and d-d pairs with s/p).
 #include "kernels_reg.cuh"
 #include "reg_dispatch.h"
 
@@ -12,11 +12,7 @@ namespace fk {
   X(1, 4, 1, 0, 2, 1)  \
   X(4, 1, 2, 1, 1, 0)  \
   X(1, 6, 1, 0, 3, 0)  \
-  X(6, 1, 3, 0, 1, 0)  \
-  X(2, 2, 1, 1, 1, 1)  \
-  X(2, 3, 1, 1, 2, 0)  \
-  X(3, 2, 2, 0, 1, 1)  \
-  X(3, 3, 2, 0, 2, 0)
+  X(6, 1, 3, 0, 1, 0)
 #include "reg_dispatch.inc"
 
 cudaError_t launch_reg_c(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st) {

@@ -194,10 +194,10 @@ def fock_build_jk_batched(handles, Ds, schwarz_thresh: float, Js, Ks, stream=Non
 
 def fock_work_stats(handle, D_host: np.ndarray, schwarz_thresh: float) -> dict:
     D_host = np.ascontiguousarray(D_host, dtype=np.float64)
-    out = np.zeros(8)
+    out = np.zeros(10)
     _check(lib().fock_work_stats(handle, _np_ptr(D_host), float(schwarz_thresh), _np_ptr(out)), "fock_work_stats")
     keys = ["quartets_schwarz", "eris_schwarz", "quartets_evaluated", "eris_evaluated", "prim_quartets",
-            "fp64_flops_model", "prim_pairs", "pairs"]
+            "flops_model", "prim_pairs", "pairs", "quartets_fp32", "flops_model_fp32"]
     return {k: float(v) for k, v in zip(keys, out)}
 
 
