@@ -50,7 +50,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: b
     if checked:
         extra_flags = tuple(extra_flags) + ("-DFOCK_BOUNDS_CHECK",)
     os.makedirs(out_dir, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh", ".inc"))]
     headers.append(os.path.join(INCLUDE, "fock.h"))
     objs, jobs = [], []
     for src in sources():

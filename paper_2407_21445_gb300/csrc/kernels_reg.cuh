@@ -363,16 +363,74 @@ __device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q, double
     quartet_reg_f64<LA, LB, LC, LD>(a, P, Q, sA, sB, sC, sD, eri_col);
 }
 
+// Warp-level work queue: the unit's kets are screened 32 at a time and the
+// surviving ones appended to an FP64 or an FP32 queue (ballot + prefix
+// popcount); each full queue is drained 32 quartets at a time, so every batch
+// runs one precision with all lanes busy and screened-out quartets cost no
+// lane time.
+template <int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void drain_reg(const KArgs &a, int P, int *q, int n, bool fp32, double *eri_col, int lane) {
+  if (lane < n) {
+    const int Q = q[lane];
+    const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
+    if (fp32)
+      quartet_reg_f32<LA, LB, LC, LD>(a, P, Q, ab.x, ab.y, cd.x, cd.y);
+    else
+      quartet_reg_f64<LA, LB, LC, LD>(a, P, Q, ab.x, ab.y, cd.x, cd.y, eri_col);
+  }
+}
+
 template <int LA, int LB, int LC, int LD>
 __global__ void __launch_bounds__(128) k_reg(KArgs a) {
   extern __shared__ __align__(16) double reg_smem[];
-  const int lane = threadIdx.x & 31;
+  __shared__ int queues[4][2][64];  // per warp: FP64 and FP32 ket queues
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double *eri_col = reg_smem + threadIdx.x;
+  int *q64 = queues[warp][0], *q32 = queues[warp][1];
+  const unsigned lt = (1u << lane) - 1u;
   for (;;) {
     const int u = next_unit(a.counter, lane);
     if (u >= a.nunits) break;
     const Unit un = a.units[u];
-    for (int Q = un.k0 + lane; Q < un.k1; Q += 32) quartet_reg<LA, LB, LC, LD>(a, un.bra, Q, eri_col);
+    const int P = un.bra;
+    const int2 ab = a.dp.ab[P];
+    int n64 = 0, n32 = 0;
+    for (int c = un.k0; c < un.k1; c += 32) {
+      const int Q = c + lane;
+      double b = -1.0;
+      if (Q < un.k1) {
+        const int2 cd = a.dp.ab[Q];
+        b = quartet_bound(a, ab.x, ab.y, cd.x, cd.y, P, Q);
+      }
+      const bool is32 = b >= 0.0 && b < a.fp32_cutoff, is64 = b >= 0.0 && !is32;
+      const unsigned m64 = __ballot_sync(0xffffffffu, is64), m32 = __ballot_sync(0xffffffffu, is32);
+      if (is64) q64[n64 + __popc(m64 & lt)] = Q;
+      if (is32) q32[n32 + __popc(m32 & lt)] = Q;
+      n64 += __popc(m64);
+      n32 += __popc(m32);
+      __syncwarp();
+      if (n64 >= 32) {
+        drain_reg<LA, LB, LC, LD>(a, P, q64, 32, false, eri_col, lane);
+        __syncwarp();
+        const int rest = lane + 32 < n64 ? q64[lane + 32] : 0;
+        __syncwarp();
+        if (lane + 32 < n64) q64[lane] = rest;
+        n64 -= 32;
+        __syncwarp();
+      }
+      if (n32 >= 32) {
+        drain_reg<LA, LB, LC, LD>(a, P, q32, 32, true, eri_col, lane);
+        __syncwarp();
+        const int rest = lane + 32 < n32 ? q32[lane + 32] : 0;
+        __syncwarp();
+        if (lane + 32 < n32) q32[lane] = rest;
+        n32 -= 32;
+        __syncwarp();
+      }
+    }
+    drain_reg<LA, LB, LC, LD>(a, P, q64, n64, false, eri_col, lane);
+    drain_reg<LA, LB, LC, LD>(a, P, q32, n32, true, eri_col, lane);
+    __syncwarp();
   }
 }
 
