@@ -48,16 +48,19 @@ def parse():
     ap.add_argument("--reg-max-l", type=int, default=0, help="largest total L served by register kernels (0 = default)")
     ap.add_argument("--fp32-cutoff", type=float, default=1e-5, help="mixed leg: FP32 below this quartet bound")
     ap.add_argument("--no-mixed-leg", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="precision of the headline leg (mixed: FP32 below --fp32-cutoff)")
     return ap.parse_args()
 
 
-def workload_config(p, st):
+def workload_config(p, st, precision="fp64"):
     c = p.meta.get("carbons", 20)
     return {"workload": f"C{c}H{2 * c + 2} zigzag alkane, 6-31G(d)-shaped synthetic basis"
             if p.meta.get("config") == 1 else p.name, "nbf": int(p.nbf), "nshell": int(len(p.basis["l"])), "schwarz_thresh": p.tau,
-            "screening": "Schwarz + six-block density (Sec. 3.2)", "precision": "fp64",
+            "screening": "Schwarz + six-block density (Sec. 3.2)",
             "eris_per_step": int(st["eris_schwarz"]), "quartets_per_step": int(st["quartets_schwarz"]),
-            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",
+            "precision": precision}
 
 
 class ClockSampler:
@@ -207,7 +210,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     p = molgen.problem(args.config, carbons=args.carbons)
-    builder = fk.JKBuilder(p.basis, p.tau, fk.make_opts(warp_scratch=args.warp_scratch, reg_max_L=args.reg_max_l))
+    prec = fk.FOCK_MIXED if args.precision == "mixed" else fk.FOCK_FP64
+    builder = fk.JKBuilder(p.basis, p.tau, fk.make_opts(precision=prec, fp32_cutoff=args.fp32_cutoff,
+                                                        warp_scratch=args.warp_scratch, reg_max_L=args.reg_max_l))
     st = builder.stats(p.D)
     nk = fk.fock_kernels_per_build(builder.handle)
     D = torch.tensor(p.D, device=dev, dtype=torch.float64)
@@ -271,7 +276,7 @@ def main():
 
     # ---- mixed-precision leg on the same workload (extra key) --------------
     mixed = None
-    if not args.no_mixed_leg:
+    if not args.no_mixed_leg and args.precision == "fp64":
         mb = fk.JKBuilder(p.basis, p.tau, fk.make_opts(precision=fk.FOCK_MIXED, fp32_cutoff=args.fp32_cutoff,
                                                       warp_scratch=args.warp_scratch, reg_max_L=args.reg_max_l))
         mst = mb.stats(p.D)
@@ -303,8 +308,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "s_per_iteration": ms * 1e-3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(p, st),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic", "config": workload_config(p, st, args.precision),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": profile_traffic(kernel_hash()),
                          "peak_note": "FP64 pipe, derived 152 SMs x 2 FMA/clk x 2.07 GHz; achieved = modelled "
