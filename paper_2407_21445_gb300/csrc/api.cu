@@ -32,7 +32,7 @@ struct Staging {  // host arrays mirroring DevPairs
   std::vector<int> eoff;
   std::vector<double> E;
   std::vector<float4> paf;
-  std::vector<float> Uf, Ef;
+  std::vector<float> Uf, Ef, Gf, shl;
 };
 
 // Device copy of a Staging set plus units: one allocation, 256-byte aligned
@@ -174,6 +174,8 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   const size_t o_U = pk.add(st.U.data(), st.U.size() * sizeof(double));
   const size_t o_eoff = pk.add(st.eoff.data(), st.eoff.size() * sizeof(int));
   const size_t o_E = pk.add(st.E.data(), st.E.size() * sizeof(double));
+  const size_t o_Gf = pk.add(st.Gf.data(), st.Gf.size() * sizeof(float));
+  const size_t o_shl = pk.add(st.shl.data(), st.shl.size() * sizeof(float));
   const size_t o_paf = pk.add(st.paf.data(), st.paf.size() * sizeof(float4));
   const size_t o_Uf = pk.add(st.Uf.data(), st.Uf.size() * sizeof(float));
   const size_t o_Ef = pk.add(st.Ef.data(), st.Ef.size() * sizeof(float));
@@ -203,6 +205,8 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   dp.eoff = (const int *)(d + o_eoff);
   dp.E = (const double *)(d + o_E);
   dp.paf = (const float4 *)(d + o_paf);
+  dp.Gf = (const float *)(d + o_Gf);
+  dp.shl = (const float *)(d + o_shl);
   dp.Uf = (const float *)(d + o_Uf);
   dp.Ef = (const float *)(d + o_Ef);
   dp.npair = (int)st.ab.size();
@@ -321,6 +325,14 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
   // ---- shells --------------------------------------------------------------
   Staging st;
   st.sxyz.assign(desc->center, desc->center + 3 * ns);
+  st.shl.resize(6 * ns);
+  for (int s = 0; s < ns; ++s)
+    for (int x = 0; x < 3; ++x) {
+      const double c = desc->center[3 * s + x];
+      const float hi = (float)c;
+      st.shl[6 * s + x] = hi;
+      st.shl[6 * s + 3 + x] = (float)(c - (double)hi);
+    }
   st.sl.assign(desc->l, desc->l + ns);
   st.sbf.resize(ns);
   int nbf = 0;
@@ -427,6 +439,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     const int P = r.idx;
     st.ab.push_back(all.ab[P]);
     st.G.push_back(Gpair[P]);
+    st.Gf.push_back((float)Gpair[P]);
     st.cls.push_back(all.cls[P]);
     st.prim.push_back(make_int2((int)st.pz.size(), r.nkeep));
     for (int i : kept_prims[P]) {
@@ -609,13 +622,15 @@ fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double sch
   const size_t dsh_bytes = sizeof(double) * (size_t)ns * ns;
   const size_t cnt_off = (dsh_bytes + 255) & ~(size_t)255;
   const size_t df_off = (cnt_off + sizeof(int) * (nt + 1) + 255) & ~(size_t)255;
-  const size_t total = mixed ? df_off + sizeof(float) * (size_t)n * n : df_off;
+  const size_t dshf_off = mixed ? (df_off + sizeof(float) * (size_t)n * n + 255) & ~(size_t)255 : df_off;
+  const size_t total = dshf_off + sizeof(float) * (size_t)ns * ns;
   char *scratch = nullptr;
   cudaError_t e = cudaMallocAsync((void **)&scratch, total, stream);
   if (e != cudaSuccess) return to_status(e);
   double *Dsh = (double *)scratch;
   int *counters = (int *)(scratch + cnt_off);
   float *Df = mixed ? (float *)(scratch + df_off) : nullptr;
+  float *Dshf = (float *)(scratch + dshf_off);
   const bool chk = sync_check();
   const char *where = "memset";
   e = cudaMemsetAsync(counters, 0, sizeof(int) * (nt + 1), stream);
@@ -623,7 +638,7 @@ fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double sch
   if (e == cudaSuccess) e = cudaMemsetAsync(K, 0, sizeof(double) * (size_t)n * n, stream);
   if (e == cudaSuccess) {
     where = "k_dprep";
-    e = launch_dprep(D, n, sp->dev.sbf, sp->dev.sl, ns, Dsh, stream, Df);
+    e = launch_dprep(D, n, sp->dev.sbf, sp->dev.sl, ns, Dsh, stream, Df, Dshf);
     if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
   }
   static char tier_name[64];
@@ -631,7 +646,7 @@ fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double sch
     snprintf(tier_name, sizeof(tier_name), "k_jk tier %zu (G=%d, smem=%zu)", t, sp->tiers[t].G, sp->tiers[t].smem);
     where = tier_name;
     e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, J, K, counters + t, stream, Df,
-                       sp->opts.fp32_cutoff);
+                       sp->opts.fp32_cutoff, Dshf);
     if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
   }
   if (e == cudaSuccess) {

@@ -82,7 +82,9 @@ struct DevPairs {
   const double *U;     // U_P sqrt(zeta) (2/sqrt(pi))^(1/2): pref = U_P U_Q / sqrt(zeta + eta)
   const int *eoff;     // offset of the primitive pair's E block
   const double *E;     // Hermite coefficients (Cartesian normalisation folded in)
-  // FP32 copies for the mixed-precision path
+  // FP32 copies for the mixed-precision path and the FP32 screening pre-test
+  const float *Gf;     // G_ab rounded to FP32
+  const float *shl;    // shell centres as FP32 hi/lo pairs: [6*s] = hx hy hz lx ly lz
   const float4 *paf;   // (P - A, zeta) with A the first shell of the canonical pair
   const float *Uf;     // U as above, FP32
   const float *Ef;     // Hermite coefficients, FP32
@@ -148,10 +150,10 @@ const float *dev_boys_f();
 const ClassTables *dev_class_tables();
 cudaError_t launch_schwarz(const DevPairs &dp, double *Gpair, double *Gprim, cudaStream_t st);
 cudaError_t launch_dprep(const double *D, int nbf, const int *sbf, const int *sl, int nshell,
-                         double *Dsh, cudaStream_t st, float *Df = nullptr);
+                         double *Dsh, cudaStream_t st, float *Df = nullptr, float *Dshf = nullptr);
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh,
                            double tau, double *J, double *K, int *counter, cudaStream_t st,
-                           const float *Df = nullptr, double fp32_cutoff = 0.0);
+                           const float *Df = nullptr, double fp32_cutoff = 0.0, const float *Dshf = nullptr);
 cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st);
 cudaError_t configure_tier(Tier &t);
 int read_and_clear_status(cudaStream_t st, int *status);

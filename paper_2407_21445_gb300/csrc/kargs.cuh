@@ -24,11 +24,32 @@ struct KArgs {
   double fp32_cutoff;  // 0 = FP64 only
   const float *Df;     // FP32 copy of D (mixed path)
   const float *boysf;  // FP32 Boys table (same layout)
+  const float *Dshf;   // FP32 shell-block maxima (screening pre-test), may be null
+  float tau_lo, tau_hi;  // tau (1 -+ 1e-4): FP32 decisions outside this band are exact
+  float fp32_cutoff_f;   // fp32_cutoff rounded to FP32
 };
 
 // Density-weighted Schwarz bound G_ab G_cd max|D| over the six blocks
 // (Sec. 3.2); returns a negative value when the quartet is screened out.
-__device__ __forceinline__ double quartet_bound(const KArgs &a, int sA, int sB, int sC, int sD, int P, int Q) {
+// The decision is taken on the FP32 units whenever both products are more
+// than 1e-4 (relative) away from tau -- FP32 rounding of the inputs and
+// products is below 1e-6 -- and in FP64 otherwise, so that it always equals
+// the FP64 decision.
+__device__ __forceinline__ float quartet_bound(const KArgs &a, int sA, int sB, int sC, int sD, int P, int Q) {
+  if (a.Dshf) {
+    const int ns = a.dp.nshell;
+    const float *Ds = a.Dshf;
+    const float gf = a.dp.Gf[P] * a.dp.Gf[Q];
+    float dm = Ds[sA * ns + sB];
+    dm = fmaxf(dm, Ds[sC * ns + sD]);
+    dm = fmaxf(dm, Ds[sA * ns + sC]);
+    dm = fmaxf(dm, Ds[sA * ns + sD]);
+    dm = fmaxf(dm, Ds[sB * ns + sC]);
+    dm = fmaxf(dm, Ds[sB * ns + sD]);
+    const float bf = gf * dm;
+    if (gf < a.tau_lo || bf < a.tau_lo) return -1.0f;
+    if (gf > a.tau_hi && bf > a.tau_hi) return bf;
+  }
   const double g = a.dp.G[P] * a.dp.G[Q];
   const int ns = a.dp.nshell;
   const double *Ds = a.Dsh;
@@ -39,21 +60,12 @@ __device__ __forceinline__ double quartet_bound(const KArgs &a, int sA, int sB, 
   dm = fmax(dm, Ds[sB * ns + sC]);
   dm = fmax(dm, Ds[sB * ns + sD]);
   const double b = g * dm;
-  return (g < a.tau || b < a.tau) ? -1.0 : b;
+  return (g < a.tau || b < a.tau) ? -1.0f : (float)b;
 }
 
 // Density-weighted Schwarz test of quartet (P|Q) (Sec. 3.2): true = skip.
 __device__ __forceinline__ bool screened(const KArgs &a, int sA, int sB, int sC, int sD, int P, int Q) {
-  const double g = a.dp.G[P] * a.dp.G[Q];
-  const int ns = a.dp.nshell;
-  const double *Ds = a.Dsh;
-  double dm = Ds[sA * ns + sB];
-  dm = fmax(dm, Ds[sC * ns + sD]);
-  dm = fmax(dm, Ds[sA * ns + sC]);
-  dm = fmax(dm, Ds[sA * ns + sD]);
-  dm = fmax(dm, Ds[sB * ns + sC]);
-  dm = fmax(dm, Ds[sB * ns + sD]);
-  return g < a.tau || g * dm < a.tau;
+  return quartet_bound(a, sA, sB, sC, sD, P, Q) < 0.0f;
 }
 
 // Next work unit for the calling warp (lane 0 draws from the tier counter).

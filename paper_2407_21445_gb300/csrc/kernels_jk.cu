@@ -347,7 +347,8 @@ __global__ void __launch_bounds__(128) k_schwarz(DevPairs dp, const double *boys
 
 // Shell-block maxima |D| (Sec. 3.2 density screening) and a finiteness check.
 __global__ void k_dprep(const double *__restrict__ D, int N, const int *__restrict__ sbf,
-                        const int *__restrict__ sl, int ns, double *__restrict__ Dsh, float *__restrict__ Df) {
+                        const int *__restrict__ sl, int ns, double *__restrict__ Dsh, float *__restrict__ Df,
+                        float *__restrict__ Dshf) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= ns * ns) return;
   const int a = idx / ns, b = idx - a * ns;
@@ -363,6 +364,7 @@ __global__ void k_dprep(const double *__restrict__ D, int N, const int *__restri
     }
   if (bad) atomicCAS(&g_status, 0, (int)FOCK_ERR_NONFINITE);
   Dsh[idx] = bad ? INFINITY : mx;
+  if (Dshf) Dshf[idx] = bad ? INFINITY : (float)mx;
 }
 
 // M <- M + M^T in place, for J (z = 0) and K (z = 1).
@@ -449,9 +451,9 @@ cudaError_t launch_schwarz(const DevPairs &dp, double *Gpair, double *Gprim, cud
 }
 
 cudaError_t launch_dprep(const double *D, int nbf, const int *sbf, const int *sl, int nshell, double *Dsh,
-                         cudaStream_t st, float *Df) {
+                         cudaStream_t st, float *Df, float *Dshf) {
   const int n = nshell * nshell;
-  k_dprep<<<(n + 255) / 256, 256, 0, st>>>(D, nbf, sbf, sl, nshell, Dsh, Df);
+  k_dprep<<<(n + 255) / 256, 256, 0, st>>>(D, nbf, sbf, sl, nshell, Dsh, Df, Dshf);
   return cudaGetLastError();
 }
 
@@ -514,9 +516,15 @@ cudaError_t configure_tier(Tier &t) {
   return cudaErrorInvalidValue;
 }
 
+static void set_screen_args(KArgs &a, double tau, const float *Dshf) {
+  a.Dshf = Dshf;
+  a.tau_lo = (float)(tau * (1.0 - 1e-4));
+  a.tau_hi = (float)(tau * (1.0 + 1e-4));
+}
+
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh, double tau,
                            double *J, double *K, int *counter, cudaStream_t st, const float *Df,
-                           double fp32_cutoff) {
+                           double fp32_cutoff, const float *Dshf) {
   if (t.nunits == 0) return cudaSuccess;
   if (t.reg_cb >= 0) {
     KArgs a;
@@ -535,8 +543,10 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
     a.boys = dev_boys();
     a.tabs = dev_class_tables();
     a.fp32_cutoff = Df ? fp32_cutoff : 0.0;
+    a.fp32_cutoff_f = (float)a.fp32_cutoff;
     a.Df = Df;
     a.boysf = dev_boys_f();
+    set_screen_args(a, tau, Dshf);
     cudaError_t e = launch_reg_a(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
     if (e == cudaErrorInvalidValue) e = launch_reg_b(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
     if (e == cudaErrorInvalidValue) e = launch_reg_c(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
@@ -572,8 +582,10 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
   a.boys = dev_boys();
   a.tabs = dev_class_tables();
   a.fp32_cutoff = 0.0;  // the group kernels evaluate every quartet in FP64
+  a.fp32_cutoff_f = 0.0f;
   a.Df = nullptr;
   a.boysf = dev_boys_f();
+  set_screen_args(a, tau, Dshf);
   const dim3 blk(32 * t.warps_per_block);
   switch (t.G) {
     case 1: k_jk<1><<<t.blocks, blk, t.smem, st>>>(a); break;

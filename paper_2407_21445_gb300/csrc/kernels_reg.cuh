@@ -244,9 +244,12 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, int P, int Q, in
   constexpr int LAB = LA + LB, L = LA + LB + LC + LD;
   constexpr int NHAB = nherm(LAB), NHL = nherm(L);
   const DevPairs &dp = a.dp;
-  const float ACx = (float)(dp.sxyz[3 * sA] - dp.sxyz[3 * sC]);
-  const float ACy = (float)(dp.sxyz[3 * sA + 1] - dp.sxyz[3 * sC + 1]);
-  const float ACz = (float)(dp.sxyz[3 * sA + 2] - dp.sxyz[3 * sC + 2]);
+  // A - C from hi/lo FP32 parts: the hi difference rounds once relative to
+  // |A - C| itself, the lo parts restore the bits the hi parts dropped
+  const float *ha = dp.shl + 6 * sA, *hc = dp.shl + 6 * sC;
+  const float ACx = (ha[0] - hc[0]) + (ha[3] - hc[3]);
+  const float ACy = (ha[1] - hc[1]) + (ha[4] - hc[4]);
+  const float ACz = (ha[2] - hc[2]) + (ha[5] - hc[5]);
   float eri[NAB * NCD];
   sfor<NAB * NCD>([&](auto i) { eri[FK_CI(i)] = 0.0f; });
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
@@ -355,9 +358,9 @@ template <int LA, int LB, int LC, int LD>
 __device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q, double *eri_col) {
   const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
   const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
-  const double b = quartet_bound(a, sA, sB, sC, sD, P, Q);
-  if (b < 0.0) return;
-  if (b < a.fp32_cutoff)
+  const float b = quartet_bound(a, sA, sB, sC, sD, P, Q);
+  if (b < 0.0f) return;
+  if (b < a.fp32_cutoff_f)
     quartet_reg_f32<LA, LB, LC, LD>(a, P, Q, sA, sB, sC, sD);
   else
     quartet_reg_f64<LA, LB, LC, LD>(a, P, Q, sA, sB, sC, sD, eri_col);
@@ -397,12 +400,12 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
     int n64 = 0, n32 = 0;
     for (int c = un.k0; c < un.k1; c += 32) {
       const int Q = c + lane;
-      double b = -1.0;
+      float b = -1.0f;
       if (Q < un.k1) {
         const int2 cd = a.dp.ab[Q];
         b = quartet_bound(a, ab.x, ab.y, cd.x, cd.y, P, Q);
       }
-      const bool is32 = b >= 0.0 && b < a.fp32_cutoff, is64 = b >= 0.0 && !is32;
+      const bool is32 = b >= 0.0f && b < a.fp32_cutoff_f, is64 = b >= 0.0f && !is32;
       const unsigned m64 = __ballot_sync(0xffffffffu, is64), m32 = __ballot_sync(0xffffffffu, is32);
       if (is64) q64[n64 + __popc(m64 & lt)] = Q;
       if (is32) q32[n32 + __popc(m32 & lt)] = Q;
