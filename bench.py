@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--carbons", type=int, default=20, help="alkane length for --config 1 (profiling cases)")
+    ap.add_argument("--nmol", type=int, default=256, help="molecules of the batched workload (--config 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warp-scratch", type=int, default=0, help="shared-memory doubles per warp (0 = library default)")
     ap.add_argument("--reg-max-l", type=int, default=0, help="largest total L served by register kernels (0 = default)")
@@ -188,6 +189,104 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, fk, torch, dev, stream, world, rank, dist):
+    """256 molecules of uneven size (TZ-shaped basis up to f) per step through
+    fock_build_jk_batched; FP64 headline plus a mixed-precision leg."""
+    import molgen
+    probs = molgen.batch_problems(args.nmol)
+    tau = probs[0].tau
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def setup(prec):
+        bs = [fk.JKBuilder(p.basis, tau, fk.make_opts(precision=prec, fp32_cutoff=args.fp32_cutoff,
+                                                     warp_scratch=args.warp_scratch, reg_max_L=args.reg_max_l))
+              for p in probs]
+        return bs
+
+    def timed(bs, Ds, Js, Ks):
+        hs = [b.handle for b in bs]
+        for _ in range(max(3, args.warmup)):
+            fk.fock_build_jk_batched(hs, Ds, tau, Js, Ks)
+        torch.cuda.synchronize(dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for s, e in evs:
+            flush.zero_()
+            s.record(stream)
+            fk.fock_build_jk_batched(hs, Ds, tau, Js, Ks)
+            e.record(stream)
+        torch.cuda.synchronize(dev)
+        return float(sum(s.elapsed_time(e) for s, e in evs)) / args.steps
+
+    Ds = [torch.tensor(p.D, device=dev) for p in probs]
+    Js = [torch.empty_like(d) for d in Ds]
+    Ks = [torch.empty_like(d) for d in Ds]
+    bs = setup(fk.FOCK_FP64)
+    stats = [b.stats(p.D) for b, p in zip(bs, probs)]
+    eris = sum(s["eris_schwarz"] for s in stats)
+    flops = sum(s["flops_model"] for s in stats)
+    if dist:
+        dist.barrier()
+    with ClockSampler(dev.index) as clk:
+        ms = timed(bs, Ds, Js, Ks)
+    assert fk.fock_stream_status() == 0
+    Jref = [j.clone() for j in Js]
+    Kref = [k.clone() for k in Ks]
+    # e2e: pinned host densities in, J and K back to pinned host, every step
+    Dh = [torch.tensor(p.D).pin_memory() for p in probs]
+    Jh = [torch.empty_like(d).pin_memory() for d in Dh]
+    Kh = [torch.empty_like(d).pin_memory() for d in Dh]
+    hs = [b.handle for b in bs]
+    e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e_s.record(stream)
+    for _ in range(args.steps):
+        for d, h in zip(Ds, Dh):
+            d.copy_(h, non_blocking=True)
+        fk.fock_build_jk_batched(hs, Ds, tau, Js, Ks)
+        for j, k, jh, kh in zip(Js, Ks, Jh, Kh):
+            jh.copy_(j, non_blocking=True)
+            kh.copy_(k, non_blocking=True)
+    e_e.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e_s.elapsed_time(e_e) / args.steps
+    nbytes = sum(d.numel() * 8 for d in Ds)
+    mixed = None
+    if not args.no_mixed_leg:
+        for b in bs:
+            b.close()
+        mbs = setup(fk.FOCK_MIXED)
+        mst = [b.stats(p.D) for b, p in zip(mbs, probs)]
+        mms = timed(mbs, Ds, Js, Ks)
+        err = max(max(float((j - jr).abs().max()), float((k - kr).abs().max()))
+                  for j, k, jr, kr in zip(Js, Ks, Jref, Kref))
+        q32 = sum(s["quartets_fp32"] for s in mst)
+        q = sum(s["quartets_evaluated"] for s in mst)
+        f32 = sum(s["flops_model_fp32"] for s in mst)
+        mixed = {"ms_per_step": mms, "value": eris / (mms * 1e-3), "unit": UNIT, "speedup_vs_fp64": ms / mms,
+                 "fp32_cutoff": args.fp32_cutoff, "max_abs_diff_vs_fp64": err,
+                 "fp32_quartet_share": q32 / max(q, 1.0), "fp32_flop_share": f32 / max(flops, 1.0),
+                 "fp64_flop_frac_of_peak": (flops - f32) / (mms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+    if rank == 0:
+        achieved = flops / (ms * 1e-3) / 1e12
+        nbf = [p.nbf for p in probs]
+        line = {"metric": METRIC, "value": world * eris / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "s_per_iteration": ms * 1e-3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": f"{len(probs)} molecules of 5-40 atoms (water clusters, alkanes, mixtures), "
+                                       "TZ-shaped synthetic basis up to f, batched build under a CUDA graph",
+                           "molecules": len(probs), "nbf_total": int(sum(nbf)), "nbf_min": int(min(nbf)),
+                           "nbf_max": int(max(nbf)), "schwarz_thresh": tau, "eris_per_step": int(eris),
+                           "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",
+                           "precision": "fp64"},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None},
+                "e2e": {"value": world * eris / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
+                        "d2h_bytes_per_step": int(2 * nbytes)},
+                "mixed": mixed, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -209,6 +308,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
+    if args.config == 3:
+        return run_batched(args, fk, torch, dev, stream, world, rank, dist)
     p = molgen.problem(args.config, carbons=args.carbons)
     prec = fk.FOCK_MIXED if args.precision == "mixed" else fk.FOCK_FP64
     builder = fk.JKBuilder(p.basis, p.tau, fk.make_opts(precision=prec, fp32_cutoff=args.fp32_cutoff,

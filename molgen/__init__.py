@@ -333,6 +333,53 @@ def problem(config: int, seed: int = 0, carbons: int = 20) -> Problem:
     return Problem(name, mol, basis, D, tau, dict(config=config, seed=seed, carbons=carbons))
 
 
+def batch_molecules(n: int = 256, seed: int = 0, min_atoms: int = 5, max_atoms: int = 40) -> list:
+    """Seeded molecules of uneven size (min_atoms..max_atoms atoms): a water
+    cluster (H2O)_m, a zigzag alkane C_kH_(2k+2) with random torsions, or a
+    non-overlapping union of one of each."""
+    rng = np.random.Generator(np.random.PCG64(30_000 + seed))
+    out = []
+    while len(out) < n:
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            mol = water_chain_cluster(int(rng.integers(2, 14)), rng)
+        elif kind == 1:
+            k = int(rng.integers(1, 13))
+            tors = rng.uniform(-np.pi, np.pi, max(0, k - 3)) if k > 3 else None
+            mol = alkane_zigzag(k, torsions=tors)
+            if _clash(mol):
+                continue
+        else:
+            k = int(rng.integers(1, 7))
+            a = alkane_zigzag(k)
+            w = water_chain_cluster(int(rng.integers(2, 6)), rng)
+            shift = (a.coords.max(axis=0) - w.coords.min(axis=0)) + np.array([6.0, 0.0, 0.0]) / BOHR_ANGSTROM
+            w = Molecule(w.symbols, w.coords + np.array([shift[0], 0.0, 0.0]))
+            mol = combine(a, w)
+        if min_atoms <= mol.natom <= max_atoms:
+            out.append(mol)
+    return out
+
+
+def _clash(mol: Molecule, dmin_ang=0.9) -> bool:
+    x = mol.coords * BOHR_ANGSTROM
+    d = np.linalg.norm(x[:, None] - x[None], axis=-1)
+    np.fill_diagonal(d, 1e9)
+    return bool(d.min() < dmin_ang)
+
+
+def batch_problems(n: int = 256, seed: int = 0, kind: str = "tz", tau: float = 1e-10) -> list:
+    """The batched workload: n seeded molecules with the triple-zeta-shaped basis
+    up to f and each its own distance-decaying density."""
+    table = basis_set(kind, seed)
+    probs = []
+    for i, mol in enumerate(batch_molecules(n, seed)):
+        basis = make_basis(mol, table)
+        probs.append(Problem(f"batch molecule {i} ({mol.natom} atoms)", mol, basis, density(basis, 1000 * seed + i),
+                             tau, dict(batch_index=i, seed=seed)))
+    return probs
+
+
 def custom_problem(mol: Molecule, kind="dz", seed=0, tau=1e-10, name="custom") -> Problem:
     basis = make_basis(mol, basis_set(kind, seed))
     return Problem(name, mol, basis, density(basis, seed), tau, dict(seed=seed))

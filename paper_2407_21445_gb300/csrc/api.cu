@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -19,21 +20,6 @@ namespace {
 
 constexpr double kPi = 3.141592653589793238462643383;
 
-struct Staging {  // host arrays mirroring DevPairs
-  std::vector<double> sxyz;
-  std::vector<int> sbf, sl;
-  std::vector<int2> ab;
-  std::vector<double> G;
-  std::vector<int2> prim;
-  std::vector<int> cls;
-  std::vector<PZ> pz;
-  std::vector<float4> pf;
-  std::vector<double> U;
-  std::vector<int> eoff;
-  std::vector<double> E;
-  std::vector<float4> paf;
-  std::vector<float> Uf, Ef, Gf, shl;
-};
 
 // Device copy of a Staging set plus units: one allocation, 256-byte aligned
 // sub-buffers.  Returns the base pointer; fills dp and unit pointers.
@@ -179,6 +165,7 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   const size_t o_paf = pk.add(st.paf.data(), st.paf.size() * sizeof(float4));
   const size_t o_Uf = pk.add(st.Uf.data(), st.Uf.size() * sizeof(float));
   const size_t o_Ef = pk.add(st.Ef.data(), st.Ef.size() * sizeof(float));
+  const size_t o_smol = pk.add(st.smol.data(), st.smol.size() * sizeof(int));
   const size_t o_units = pk.add(units.data(), units.size() * sizeof(Unit));
   const size_t total = (pk.off + 255) & ~(size_t)255;
   char *d = nullptr;
@@ -206,6 +193,7 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   dp.E = (const double *)(d + o_E);
   dp.paf = (const float4 *)(d + o_paf);
   dp.Gf = (const float *)(d + o_Gf);
+  dp.smol = st.smol.empty() ? nullptr : (const int *)(d + o_smol);
   dp.shl = (const float *)(d + o_shl);
   dp.Uf = (const float *)(d + o_Uf);
   dp.Ef = (const float *)(d + o_Ef);
@@ -219,6 +207,13 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
 }
 
 }  // namespace
+
+namespace fk {
+fock_status upload_staging(const Staging &st, const std::vector<Unit> &units, void **base, DevPairs &dp,
+                           Unit **d_units, size_t *bytes, cudaStream_t stream) {
+  return upload(st, units, base, dp, d_units, bytes, stream);
+}
+}  // namespace fk
 
 extern "C" {
 
@@ -546,6 +541,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     tier.G = keys[ki].G;
     tier.reg_cb = keys[ki].cb;
     tier.reg_ck = keys[ki].ck;
+    tier.sb = keys[ki].sb;
     int stride = 1;
     const int chunk = (32 / tier.G) * 8;
     const size_t first = all_units.size();
@@ -608,6 +604,9 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
   sp->h_cls = st.cls;
   sp->h_units = std::move(all_units);
   sp->h_unit_tier = std::move(unit_tier);
+  sp->host = std::move(st);
+  static std::atomic<unsigned long long> next_serial{1};
+  sp->serial = next_serial++;
   *out = sp;
   return FOCK_OK;
 }
@@ -660,16 +659,6 @@ fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double sch
     where = "cudaFreeAsync";
   }
   return to_status(e, where);
-}
-
-fock_status fock_build_jk_batched(const fock_shellpairs *const *bases, int32_t nmol, const double *const *D,
-                                  double schwarz_thresh, double *const *J, double *const *K, cudaStream_t stream) {
-  if (!bases || nmol < 0 || !D || !J || !K) return FOCK_ERR_INVALID_ARG;
-  for (int i = 0; i < nmol; ++i) {
-    fock_status s = fock_build_jk(bases[i], D[i], schwarz_thresh, J[i], K[i], stream);
-    if (s != FOCK_OK) return s;
-  }
-  return FOCK_OK;
 }
 
 fock_status fock_stream_status(cudaStream_t stream) {

@@ -88,9 +88,39 @@ struct DevPairs {
   const float4 *paf;   // (P - A, zeta) with A the first shell of the canonical pair
   const float *Uf;     // U as above, FP32
   const float *Ef;     // Hermite coefficients, FP32
+  const int *smol;     // shell -> molecule of a batch (null for one molecule)
   int nshell, nbf, npair;
   int nprim_total;
   long long nE_total;
+};
+
+// Per-molecule entry of a batched build (device table, rewritten per call).
+struct MolEntry {
+  const double *D;
+  double *J;
+  double *K;
+  const float *Df;     // FP32 copy of D (mixed path) or null
+  long long dsh_off;   // offset of the molecule's nshell^2 block maxima
+  long long n2_off;    // offset of the molecule's N^2 block in packed per-call arrays
+  int N, s0, ns, pad;  // functions, first shell, shells
+};
+
+// Host arrays mirroring DevPairs (the compact, sorted data of a handle).
+struct Staging {
+  std::vector<double> sxyz;
+  std::vector<int> sbf, sl;
+  std::vector<int2> ab;
+  std::vector<double> G;
+  std::vector<int2> prim;
+  std::vector<int> cls;
+  std::vector<PZ> pz;
+  std::vector<float4> pf;
+  std::vector<double> U;
+  std::vector<int> eoff;
+  std::vector<double> E;
+  std::vector<float4> paf;
+  std::vector<float> Uf, Ef, Gf, shl;
+  std::vector<int> smol;
 };
 
 // One unit of work: bra pair index, ket pair index range [k0, k1).
@@ -101,6 +131,7 @@ struct Unit {
 struct Tier {
   int reg_cb = -1;      // >= 0: per-class register kernel for (bra class, ket class)
   int reg_ck = -1;
+  int sb = 0;           // scratch bucket of a full-warp group tier
   int G;                // lanes per quartet (group kernel)
   int stride;           // scratch doubles per group
   int warps_per_block;
@@ -126,6 +157,8 @@ struct fock_shellpairs {
   std::vector<int> h_cls;
   std::vector<fk::Unit> h_units;      // all tiers, concatenated
   std::vector<int> h_unit_tier;
+  fk::Staging host;                   // compact pair data (merged into batch plans)
+  unsigned long long serial = 0;      // unique id (batch plan cache key)
   // device allocations
   void *d_block = nullptr;            // one allocation holding all pair arrays
   fk::DevPairs dev{};
@@ -155,6 +188,16 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
                            double tau, double *J, double *K, int *counter, cudaStream_t st,
                            const float *Df = nullptr, double fp32_cutoff = 0.0, const float *Dshf = nullptr);
 cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st);
+// batched variants (one launch over every molecule of a batch)
+cudaError_t launch_zero_batch(const MolEntry *mt, const long long *n2_prefix, int nmol, long long total,
+                              cudaStream_t st);
+cudaError_t launch_dprep_batch(const MolEntry *mt, const long long *dsh_prefix, int nmol, long long total,
+                               const int *sbf, const int *sl, double *Dsh, float *Dshf, cudaStream_t st);
+cudaError_t launch_symmetrize_batch(const MolEntry *mt, const long long *n2_prefix, int nmol, long long total,
+                                    cudaStream_t st);
+cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEntry *mt, const double *Dsh,
+                                 const float *Dshf, double tau, int *counter, cudaStream_t st,
+                                 double fp32_cutoff);
 cudaError_t configure_tier(Tier &t);
 int read_and_clear_status(cudaStream_t st, int *status);
 int read_bounds(long long out[2]);

@@ -27,7 +27,47 @@ struct KArgs {
   const float *Dshf;   // FP32 shell-block maxima (screening pre-test), may be null
   float tau_lo, tau_hi;  // tau (1 -+ 1e-4): FP32 decisions outside this band are exact
   float fp32_cutoff_f;   // fp32_cutoff rounded to FP32
+  const MolEntry *mt;  // batched build: per-molecule table (null for one molecule)
 };
+
+// The molecule a quartet belongs to: its D, J, K, dimension and the block of
+// the shell-block maxima, with shell indices made molecule-local.
+struct MolView {
+  const double *D;
+  double *J;
+  double *K;
+  const float *Df;
+  const double *Dsh;
+  const float *Dshf;
+  int N, s0, ns;
+};
+
+__device__ __forceinline__ MolView mol_view(const KArgs &a, int shell) {
+  MolView v;
+  if (a.mt == nullptr) {
+    v.D = a.D;
+    v.J = a.J;
+    v.K = a.K;
+    v.Df = a.Df;
+    v.Dsh = a.Dsh;
+    v.Dshf = a.Dshf;
+    v.N = a.dp.nbf;
+    v.s0 = 0;
+    v.ns = a.dp.nshell;
+  } else {
+    const MolEntry &m = a.mt[a.dp.smol[shell]];
+    v.D = m.D;
+    v.J = m.J;
+    v.K = m.K;
+    v.Df = m.Df;
+    v.Dsh = a.Dsh + m.dsh_off;
+    v.Dshf = a.Dshf ? a.Dshf + m.dsh_off : nullptr;
+    v.N = m.N;
+    v.s0 = m.s0;
+    v.ns = m.ns;
+  }
+  return v;
+}
 
 // Density-weighted Schwarz bound G_ab G_cd max|D| over the six blocks
 // (Sec. 3.2); returns a negative value when the quartet is screened out.
@@ -35,10 +75,15 @@ struct KArgs {
 // than 1e-4 (relative) away from tau -- FP32 rounding of the inputs and
 // products is below 1e-6 -- and in FP64 otherwise, so that it always equals
 // the FP64 decision.
-__device__ __forceinline__ float quartet_bound(const KArgs &a, int sA, int sB, int sC, int sD, int P, int Q) {
-  if (a.Dshf) {
-    const int ns = a.dp.nshell;
-    const float *Ds = a.Dshf;
+__device__ __forceinline__ float quartet_bound(const KArgs &a, const MolView &mv, int sA, int sB, int sC, int sD,
+                                               int P, int Q) {
+  sA -= mv.s0;
+  sB -= mv.s0;
+  sC -= mv.s0;
+  sD -= mv.s0;
+  if (mv.Dshf) {
+    const int ns = mv.ns;
+    const float *Ds = mv.Dshf;
     const float gf = a.dp.Gf[P] * a.dp.Gf[Q];
     float dm = Ds[sA * ns + sB];
     dm = fmaxf(dm, Ds[sC * ns + sD]);
@@ -51,8 +96,8 @@ __device__ __forceinline__ float quartet_bound(const KArgs &a, int sA, int sB, i
     if (gf > a.tau_hi && bf > a.tau_hi) return bf;
   }
   const double g = a.dp.G[P] * a.dp.G[Q];
-  const int ns = a.dp.nshell;
-  const double *Ds = a.Dsh;
+  const int ns = mv.ns;
+  const double *Ds = mv.Dsh;
   double dm = Ds[sA * ns + sB];
   dm = fmax(dm, Ds[sC * ns + sD]);
   dm = fmax(dm, Ds[sA * ns + sC]);
@@ -64,8 +109,9 @@ __device__ __forceinline__ float quartet_bound(const KArgs &a, int sA, int sB, i
 }
 
 // Density-weighted Schwarz test of quartet (P|Q) (Sec. 3.2): true = skip.
-__device__ __forceinline__ bool screened(const KArgs &a, int sA, int sB, int sC, int sD, int P, int Q) {
-  return quartet_bound(a, sA, sB, sC, sD, P, Q) < 0.0f;
+__device__ __forceinline__ bool screened(const KArgs &a, const MolView &mv, int sA, int sB, int sC, int sD, int P,
+                                         int Q) {
+  return quartet_bound(a, mv, sA, sB, sC, sD, P, Q) < 0.0f;
 }
 
 // Next work unit for the calling warp (lane 0 draws from the tier counter).

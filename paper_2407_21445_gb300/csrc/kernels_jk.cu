@@ -24,6 +24,7 @@
 // comparatively free and are spent freely to keep FP64 lanes busy.
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include "device_common.cuh"
 #include "kargs.cuh"
@@ -110,7 +111,8 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
   const int2 ab = dp.ab[P], cd = dp.ab[Q];
   const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
   // density-weighted Schwarz screening over the six shell blocks (Sec. 3.2)
-  if (screened(a, sA, sB, sC, sD, P, Q)) return;
+  const MolView mv = mol_view(a, sA);
+  if (screened(a, mv, sA, sB, sC, sD, P, Q)) return;
 
   const int cb = dp.cls[P], ck = dp.cls[Q];
   const int la = dp.sl[sA], lb = dp.sl[sB], lc = dp.sl[sC], ld = dp.sl[sD];
@@ -191,9 +193,9 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
   if (sA == sB) fac *= 0.5;
   if (sC == sD) fac *= 0.5;
   if (P == Q) fac *= 0.5;
-  const int N = dp.nbf;
+  const int N = mv.N;
   const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
-  const double *Dm = a.D;
+  const double *Dm = mv.D;
   const double fac2 = 2.0 * fac;
   const int n1 = nab, n2 = n1 + ncd, n3 = n2 + na * nc, n4 = n3 + na * nd, n5 = n4 + nb * nc,
             n6 = n5 + nb * nd;
@@ -205,41 +207,41 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
       const double *e = eri + (size_t)o * ncd;
       for (int ic = 0; ic < nc; ++ic)
         for (int id = 0; id < nd; ++id) s = fma(e[ic * nd + id], Dm[(size_t)(fc + ic) * N + fd + id], s);
-      dst = a.J + (size_t)(fa + ia) * N + fb + ib;
+      dst = mv.J + (size_t)(fa + ia) * N + fb + ib;
       s *= fac2;
     } else if (o < n2) {
       const int k = o - n1, ic = k / nd, id = k - ic * nd;
       for (int ia = 0; ia < na; ++ia)
         for (int ib = 0; ib < nb; ++ib) s = fma(eri[(ia * nb + ib) * ncd + k], Dm[(size_t)(fa + ia) * N + fb + ib], s);
-      dst = a.J + (size_t)(fc + ic) * N + fd + id;
+      dst = mv.J + (size_t)(fc + ic) * N + fd + id;
       s *= fac2;
     } else if (o < n3) {  // K_ac += (ab|cd) D_bd
       const int k = o - n2, ia = k / nc, ic = k - ia * nc;
       for (int ib = 0; ib < nb; ++ib)
         for (int id = 0; id < nd; ++id)
           s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fb + ib) * N + fd + id], s);
-      dst = a.K + (size_t)(fa + ia) * N + fc + ic;
+      dst = mv.K + (size_t)(fa + ia) * N + fc + ic;
       s *= fac;
     } else if (o < n4) {  // K_ad += (ab|cd) D_bc
       const int k = o - n3, ia = k / nd, id = k - ia * nd;
       for (int ib = 0; ib < nb; ++ib)
         for (int ic = 0; ic < nc; ++ic)
           s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fb + ib) * N + fc + ic], s);
-      dst = a.K + (size_t)(fa + ia) * N + fd + id;
+      dst = mv.K + (size_t)(fa + ia) * N + fd + id;
       s *= fac;
     } else if (o < n5) {  // K_bc += (ab|cd) D_ad
       const int k = o - n4, ib = k / nc, ic = k - ib * nc;
       for (int ia = 0; ia < na; ++ia)
         for (int id = 0; id < nd; ++id)
           s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fa + ia) * N + fd + id], s);
-      dst = a.K + (size_t)(fb + ib) * N + fc + ic;
+      dst = mv.K + (size_t)(fb + ib) * N + fc + ic;
       s *= fac;
     } else {  // K_bd += (ab|cd) D_ac
       const int k = o - n5, ib = k / nd, id = k - ib * nd;
       for (int ia = 0; ia < na; ++ia)
         for (int ic = 0; ic < nc; ++ic)
           s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fa + ia) * N + fc + ic], s);
-      dst = a.K + (size_t)(fb + ib) * N + fd + id;
+      dst = mv.K + (size_t)(fb + ib) * N + fd + id;
       s *= fac;
     }
     atomicAdd(dst, s);
@@ -383,6 +385,101 @@ __global__ void k_symmetrize(double *J, double *K, int n) {
 }
 
 // --------------------------------------------------------------------------
+// batched builds: one launch over every molecule (packed index spaces)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int find_mol(const long long *prefix, int nmol, long long idx) {
+  int lo = 0, hi = nmol;  // prefix[lo] <= idx < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= idx)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_zero_batch(const MolEntry *__restrict__ mt, const long long *__restrict__ n2p, int nmol,
+                             long long total) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m = find_mol(n2p, nmol, idx);
+    const long long r = idx - n2p[m];
+    mt[m].J[r] = 0.0;
+    mt[m].K[r] = 0.0;
+  }
+}
+
+__global__ void k_dprep_batch(const MolEntry *__restrict__ mt, const long long *__restrict__ dshp, int nmol,
+                              long long total, const int *__restrict__ sbf, const int *__restrict__ sl,
+                              double *__restrict__ Dsh, float *__restrict__ Dshf) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m = find_mol(dshp, nmol, idx);
+    const MolEntry &e = mt[m];
+    const int r = (int)(idx - dshp[m]);
+    const int a = e.s0 + r / e.ns, b = e.s0 + r % e.ns;
+    const int fa = sbf[a], fb = sbf[b], na = ncart(sl[a]), nb = ncart(sl[b]);
+    double mx = 0.0;
+    bool bad = false;
+    for (int i = 0; i < na; ++i)
+      for (int j = 0; j < nb; ++j) {
+        const size_t o = (size_t)(fa + i) * e.N + fb + j;
+        const double v = e.D[o];
+        if (e.Df) const_cast<float *>(e.Df)[o] = (float)v;
+        if (!isfinite(v)) bad = true;
+        mx = fmax(mx, fabs(v));
+      }
+    if (bad) atomicCAS(&g_status, 0, (int)FOCK_ERR_NONFINITE);
+    Dsh[idx] = bad ? INFINITY : mx;
+    Dshf[idx] = bad ? INFINITY : (float)mx;
+  }
+}
+
+__global__ void k_symmetrize_batch(const MolEntry *__restrict__ mt, const long long *__restrict__ n2p, int nmol,
+                                   long long total) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m = find_mol(n2p, nmol, idx);
+    const MolEntry &e = mt[m];
+    const int r = (int)(idx - n2p[m]);
+    const int i = r / e.N, j = r % e.N;
+    if (i > j) continue;
+    for (int z = 0; z < 2; ++z) {
+      double *M = z == 0 ? e.J : e.K;
+      if (i == j) {
+        M[(size_t)i * e.N + i] *= 2.0;
+      } else {
+        const double s = M[(size_t)i * e.N + j] + M[(size_t)j * e.N + i];
+        M[(size_t)i * e.N + j] = s;
+        M[(size_t)j * e.N + i] = s;
+      }
+    }
+  }
+}
+
+static int grid_for(long long total) {
+  long long b = (total + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b > 0 ? b : 1);
+}
+
+cudaError_t launch_zero_batch(const MolEntry *mt, const long long *n2p, int nmol, long long total, cudaStream_t st) {
+  k_zero_batch<<<grid_for(total), 256, 0, st>>>(mt, n2p, nmol, total);
+  return cudaGetLastError();
+}
+cudaError_t launch_dprep_batch(const MolEntry *mt, const long long *dshp, int nmol, long long total, const int *sbf,
+                               const int *sl, double *Dsh, float *Dshf, cudaStream_t st) {
+  k_dprep_batch<<<grid_for(total), 256, 0, st>>>(mt, dshp, nmol, total, sbf, sl, Dsh, Dshf);
+  return cudaGetLastError();
+}
+cudaError_t launch_symmetrize_batch(const MolEntry *mt, const long long *n2p, int nmol, long long total,
+                                    cudaStream_t st) {
+  k_symmetrize_batch<<<grid_for(total), 256, 0, st>>>(mt, n2p, nmol, total);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
 // host-side launch helpers
 // --------------------------------------------------------------------------
 
@@ -516,6 +613,20 @@ cudaError_t configure_tier(Tier &t) {
   return cudaErrorInvalidValue;
 }
 
+// The dynamic shared-memory limit is a per-function attribute shared by
+// every handle; raise it to this tier's need before launching.
+static cudaError_t set_group_smem(const Tier &t) {
+  switch (t.G) {
+    case 1: return cudaFuncSetAttribute(k_jk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+    case 2: return cudaFuncSetAttribute(k_jk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+    case 4: return cudaFuncSetAttribute(k_jk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+    case 8: return cudaFuncSetAttribute(k_jk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+    case 16: return cudaFuncSetAttribute(k_jk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+    case 32: return cudaFuncSetAttribute(k_jk<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+  }
+  return cudaErrorInvalidValue;
+}
+
 static void set_screen_args(KArgs &a, double tau, const float *Dshf) {
   a.Dshf = Dshf;
   a.tau_lo = (float)(tau * (1.0 - 1e-4));
@@ -542,6 +653,7 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
     a.stride = 0;
     a.boys = dev_boys();
     a.tabs = dev_class_tables();
+    a.mt = nullptr;
     a.fp32_cutoff = Df ? fp32_cutoff : 0.0;
     a.fp32_cutoff_f = (float)a.fp32_cutoff;
     a.Df = Df;
@@ -553,18 +665,7 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
     if (e == cudaErrorInvalidValue) e = launch_reg_d(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
     return e;
   }
-  // The dynamic shared-memory limit is a per-function attribute shared by
-  // every handle; raise it to this tier's need before launching.
-  cudaError_t ae = cudaSuccess;
-  switch (t.G) {
-    case 1: ae = cudaFuncSetAttribute(k_jk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
-    case 2: ae = cudaFuncSetAttribute(k_jk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
-    case 4: ae = cudaFuncSetAttribute(k_jk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
-    case 8: ae = cudaFuncSetAttribute(k_jk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
-    case 16: ae = cudaFuncSetAttribute(k_jk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
-    case 32: ae = cudaFuncSetAttribute(k_jk<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem); break;
-    default: return cudaErrorInvalidValue;
-  }
+  cudaError_t ae = set_group_smem(t);
   if (ae != cudaSuccess) return ae;
   KArgs a;
   a.dp = dp;
@@ -581,6 +682,7 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
   a.stride = t.stride;
   a.boys = dev_boys();
   a.tabs = dev_class_tables();
+  a.mt = nullptr;
   a.fp32_cutoff = 0.0;  // the group kernels evaluate every quartet in FP64
   a.fp32_cutoff_f = 0.0f;
   a.Df = nullptr;
@@ -594,6 +696,50 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
     case 8: k_jk<8><<<t.blocks, blk, t.smem, st>>>(a); break;
     case 16: k_jk<16><<<t.blocks, blk, t.smem, st>>>(a); break;
     case 32: k_jk<32><<<t.blocks, blk, t.smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// One tier of a batched build: same kernels, per-molecule D/J/K from mt.
+cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEntry *mt, const double *Dsh,
+                                 const float *Dshf, double tau, int *counter, cudaStream_t st, double fp32_cutoff) {
+  if (t.nunits == 0) return cudaSuccess;
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.dp = dp;
+  a.nprimtot = dp.nprim_total;
+  a.nEtot = dp.nE_total;
+  a.Dsh = Dsh;
+  a.tau = tau;
+  a.units = t.d_units;
+  a.nunits = t.nunits;
+  a.counter = counter;
+  a.stride = t.stride;
+  a.boys = dev_boys();
+  a.tabs = dev_class_tables();
+  a.boysf = dev_boys_f();
+  a.mt = mt;
+  a.fp32_cutoff = t.reg_cb >= 0 ? fp32_cutoff : 0.0;
+  a.fp32_cutoff_f = (float)a.fp32_cutoff;
+  set_screen_args(a, tau, Dshf);
+  const int threads = 32 * t.warps_per_block;
+  if (t.reg_cb >= 0) {
+    cudaError_t e = launch_reg_a(t.reg_cb, t.reg_ck, a, t.blocks, threads, st);
+    if (e == cudaErrorInvalidValue) e = launch_reg_b(t.reg_cb, t.reg_ck, a, t.blocks, threads, st);
+    if (e == cudaErrorInvalidValue) e = launch_reg_c(t.reg_cb, t.reg_ck, a, t.blocks, threads, st);
+    if (e == cudaErrorInvalidValue) e = launch_reg_d(t.reg_cb, t.reg_ck, a, t.blocks, threads, st);
+    return e;
+  }
+  cudaError_t ae = set_group_smem(t);
+  if (ae != cudaSuccess) return ae;
+  switch (t.G) {
+    case 1: k_jk<1><<<t.blocks, threads, t.smem, st>>>(a); break;
+    case 2: k_jk<2><<<t.blocks, threads, t.smem, st>>>(a); break;
+    case 4: k_jk<4><<<t.blocks, threads, t.smem, st>>>(a); break;
+    case 8: k_jk<8><<<t.blocks, threads, t.smem, st>>>(a); break;
+    case 16: k_jk<16><<<t.blocks, threads, t.smem, st>>>(a); break;
+    case 32: k_jk<32><<<t.blocks, threads, t.smem, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -113,8 +113,8 @@ __host__ __device__ constexpr int reg_smem_bytes(int threads) {
 }
 
 template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void quartet_reg_f64(const KArgs &a, int P, int Q, int sA, int sB, int sC, int sD,
-                                                double *eri_col) {
+__device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &mv, int P, int Q, int sA, int sB,
+                                                int sC, int sD, double *eri_col) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
   constexpr int NAB = NA * NB, NCD = NC * ND;
   constexpr int LAB = LA + LB, L = LA + LB + LC + LD;
@@ -189,46 +189,48 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, int P, int Q, in
   if (sC == sD) fac *= 0.5;
   if (P == Q) fac *= 0.5;
   const double fac2 = 2.0 * fac;
-  const int N = dp.nbf;
+  const int N = mv.N;
   const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
-  const double *__restrict__ Dm = a.D;
+  const double *__restrict__ Dm = mv.D;
+  double *__restrict__ Jm = mv.J;
+  double *__restrict__ Km = mv.K;
   auto E4 = [&](int ia, int ib, int ic, int id) -> double { return eri_at((ia * NB + ib) * NCD + ic * ND + id); };
   auto Dv = [&](int r, int c) -> double { return __ldg(Dm + (size_t)r * N + c); };
   sfor<NAB>([&](auto k) {  // J_ab += (ab|cd) D_cd
     constexpr int ia = FK_CI(k) / NB, ib = FK_CI(k) % NB;
     double s = 0.0;
     sfor<NCD>([&](auto m) { s = fma(E4(ia, ib, FK_CI(m) / ND, FK_CI(m) % ND), Dv(fc + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
-    atomicAdd(a.J + (size_t)(fa + ia) * N + fb + ib, fac2 * s);
+    atomicAdd(Jm + (size_t)(fa + ia) * N + fb + ib, fac2 * s);
   });
   sfor<NCD>([&](auto k) {  // J_cd += (ab|cd) D_ab
     constexpr int ic = FK_CI(k) / ND, id = FK_CI(k) % ND;
     double s = 0.0;
     sfor<NAB>([&](auto m) { s = fma(E4(FK_CI(m) / NB, FK_CI(m) % NB, ic, id), Dv(fa + FK_CI(m) / NB, fb + FK_CI(m) % NB), s); });
-    atomicAdd(a.J + (size_t)(fc + ic) * N + fd + id, fac2 * s);
+    atomicAdd(Jm + (size_t)(fc + ic) * N + fd + id, fac2 * s);
   });
   sfor<NA * NC>([&](auto k) {  // K_ac += (ab|cd) D_bd
     constexpr int ia = FK_CI(k) / NC, ic = FK_CI(k) % NC;
     double s = 0.0;
     sfor<NB * ND>([&](auto m) { s = fma(E4(ia, FK_CI(m) / ND, ic, FK_CI(m) % ND), Dv(fb + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
-    atomicAdd(a.K + (size_t)(fa + ia) * N + fc + ic, fac * s);
+    atomicAdd(Km + (size_t)(fa + ia) * N + fc + ic, fac * s);
   });
   sfor<NA * ND>([&](auto k) {  // K_ad += (ab|cd) D_bc
     constexpr int ia = FK_CI(k) / ND, id = FK_CI(k) % ND;
     double s = 0.0;
     sfor<NB * NC>([&](auto m) { s = fma(E4(ia, FK_CI(m) / NC, FK_CI(m) % NC, id), Dv(fb + FK_CI(m) / NC, fc + FK_CI(m) % NC), s); });
-    atomicAdd(a.K + (size_t)(fa + ia) * N + fd + id, fac * s);
+    atomicAdd(Km + (size_t)(fa + ia) * N + fd + id, fac * s);
   });
   sfor<NB * NC>([&](auto k) {  // K_bc += (ab|cd) D_ad
     constexpr int ib = FK_CI(k) / NC, ic = FK_CI(k) % NC;
     double s = 0.0;
     sfor<NA * ND>([&](auto m) { s = fma(E4(FK_CI(m) / ND, ib, ic, FK_CI(m) % ND), Dv(fa + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
-    atomicAdd(a.K + (size_t)(fb + ib) * N + fc + ic, fac * s);
+    atomicAdd(Km + (size_t)(fb + ib) * N + fc + ic, fac * s);
   });
   sfor<NB * ND>([&](auto k) {  // K_bd += (ab|cd) D_ac
     constexpr int ib = FK_CI(k) / ND, id = FK_CI(k) % ND;
     double s = 0.0;
     sfor<NA * NC>([&](auto m) { s = fma(E4(FK_CI(m) / NC, ib, FK_CI(m) % NC, id), Dv(fa + FK_CI(m) / NC, fc + FK_CI(m) % NC), s); });
-    atomicAdd(a.K + (size_t)(fb + ib) * N + fd + id, fac * s);
+    atomicAdd(Km + (size_t)(fb + ib) * N + fd + id, fac * s);
   });
 }
 
@@ -238,7 +240,8 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, int P, int Q, in
 // pair's first shell so that P - Q keeps its precision; each digested J/K
 // element is converted exactly to FP64 and accumulated in FP64.
 template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void quartet_reg_f32(const KArgs &a, int P, int Q, int sA, int sB, int sC, int sD) {
+__device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &mv, int P, int Q, int sA, int sB,
+                                                int sC, int sD) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
   constexpr int NAB = NA * NB, NCD = NC * ND;
   constexpr int LAB = LA + LB, L = LA + LB + LC + LD;
@@ -309,62 +312,53 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, int P, int Q, in
   if (sC == sD) fac *= 0.5f;
   if (P == Q) fac *= 0.5f;
   const float fac2 = 2.0f * fac;
-  const int N = dp.nbf;
+  const int N = mv.N;
   const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
-  const float *__restrict__ Dm = a.Df;
+  const float *__restrict__ Dm = mv.Df;
+  double *__restrict__ Jm = mv.J;
+  double *__restrict__ Km = mv.K;
   auto E4 = [&](int ia, int ib, int ic, int id) -> float { return eri[(ia * NB + ib) * NCD + ic * ND + id]; };
   auto Dv = [&](int r, int c) -> float { return __ldg(Dm + (size_t)r * N + c); };
   sfor<NAB>([&](auto k) {
     constexpr int ia = FK_CI(k) / NB, ib = FK_CI(k) % NB;
     float s = 0.0f;
     sfor<NCD>([&](auto m) { s = fmaf(E4(ia, ib, FK_CI(m) / ND, FK_CI(m) % ND), Dv(fc + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
-    atomicAdd(a.J + (size_t)(fa + ia) * N + fb + ib, f2d_any(fac2 * s));
+    atomicAdd(Jm + (size_t)(fa + ia) * N + fb + ib, f2d_any(fac2 * s));
   });
   sfor<NCD>([&](auto k) {
     constexpr int ic = FK_CI(k) / ND, id = FK_CI(k) % ND;
     float s = 0.0f;
     sfor<NAB>([&](auto m) { s = fmaf(E4(FK_CI(m) / NB, FK_CI(m) % NB, ic, id), Dv(fa + FK_CI(m) / NB, fb + FK_CI(m) % NB), s); });
-    atomicAdd(a.J + (size_t)(fc + ic) * N + fd + id, f2d_any(fac2 * s));
+    atomicAdd(Jm + (size_t)(fc + ic) * N + fd + id, f2d_any(fac2 * s));
   });
   sfor<NA * NC>([&](auto k) {
     constexpr int ia = FK_CI(k) / NC, ic = FK_CI(k) % NC;
     float s = 0.0f;
     sfor<NB * ND>([&](auto m) { s = fmaf(E4(ia, FK_CI(m) / ND, ic, FK_CI(m) % ND), Dv(fb + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
-    atomicAdd(a.K + (size_t)(fa + ia) * N + fc + ic, f2d_any(fac * s));
+    atomicAdd(Km + (size_t)(fa + ia) * N + fc + ic, f2d_any(fac * s));
   });
   sfor<NA * ND>([&](auto k) {
     constexpr int ia = FK_CI(k) / ND, id = FK_CI(k) % ND;
     float s = 0.0f;
     sfor<NB * NC>([&](auto m) { s = fmaf(E4(ia, FK_CI(m) / NC, FK_CI(m) % NC, id), Dv(fb + FK_CI(m) / NC, fc + FK_CI(m) % NC), s); });
-    atomicAdd(a.K + (size_t)(fa + ia) * N + fd + id, f2d_any(fac * s));
+    atomicAdd(Km + (size_t)(fa + ia) * N + fd + id, f2d_any(fac * s));
   });
   sfor<NB * NC>([&](auto k) {
     constexpr int ib = FK_CI(k) / NC, ic = FK_CI(k) % NC;
     float s = 0.0f;
     sfor<NA * ND>([&](auto m) { s = fmaf(E4(FK_CI(m) / ND, ib, ic, FK_CI(m) % ND), Dv(fa + FK_CI(m) / ND, fd + FK_CI(m) % ND), s); });
-    atomicAdd(a.K + (size_t)(fb + ib) * N + fc + ic, f2d_any(fac * s));
+    atomicAdd(Km + (size_t)(fb + ib) * N + fc + ic, f2d_any(fac * s));
   });
   sfor<NB * ND>([&](auto k) {
     constexpr int ib = FK_CI(k) / ND, id = FK_CI(k) % ND;
     float s = 0.0f;
     sfor<NA * NC>([&](auto m) { s = fmaf(E4(FK_CI(m) / NC, ib, FK_CI(m) % NC, id), Dv(fa + FK_CI(m) / NC, fc + FK_CI(m) % NC), s); });
-    atomicAdd(a.K + (size_t)(fb + ib) * N + fd + id, f2d_any(fac * s));
+    atomicAdd(Km + (size_t)(fb + ib) * N + fd + id, f2d_any(fac * s));
   });
 }
 
 // One quartet: screening, then the FP32 path below the mixed-precision
 // cutoff (0 in the FP64 mode) or the FP64 path.
-template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q, double *eri_col) {
-  const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
-  const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
-  const float b = quartet_bound(a, sA, sB, sC, sD, P, Q);
-  if (b < 0.0f) return;
-  if (b < a.fp32_cutoff_f)
-    quartet_reg_f32<LA, LB, LC, LD>(a, P, Q, sA, sB, sC, sD);
-  else
-    quartet_reg_f64<LA, LB, LC, LD>(a, P, Q, sA, sB, sC, sD, eri_col);
-}
 
 // Warp-level work queue: the unit's kets are screened 32 at a time and the
 // surviving ones appended to an FP64 or an FP32 queue (ballot + prefix
@@ -372,14 +366,15 @@ __device__ __forceinline__ void quartet_reg(const KArgs &a, int P, int Q, double
 // runs one precision with all lanes busy and screened-out quartets cost no
 // lane time.
 template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void drain_reg(const KArgs &a, int P, int *q, int n, bool fp32, double *eri_col, int lane) {
+__device__ __forceinline__ void drain_reg(const KArgs &a, const MolView &mv, int P, int *q, int n, bool fp32,
+                                          double *eri_col, int lane) {
   if (lane < n) {
     const int Q = q[lane];
     const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
     if (fp32)
-      quartet_reg_f32<LA, LB, LC, LD>(a, P, Q, ab.x, ab.y, cd.x, cd.y);
+      quartet_reg_f32<LA, LB, LC, LD>(a, mv, P, Q, ab.x, ab.y, cd.x, cd.y);
     else
-      quartet_reg_f64<LA, LB, LC, LD>(a, P, Q, ab.x, ab.y, cd.x, cd.y, eri_col);
+      quartet_reg_f64<LA, LB, LC, LD>(a, mv, P, Q, ab.x, ab.y, cd.x, cd.y, eri_col);
   }
 }
 
@@ -397,13 +392,14 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
     const Unit un = a.units[u];
     const int P = un.bra;
     const int2 ab = a.dp.ab[P];
+    const MolView mv = mol_view(a, ab.x);
     int n64 = 0, n32 = 0;
     for (int c = un.k0; c < un.k1; c += 32) {
       const int Q = c + lane;
       float b = -1.0f;
       if (Q < un.k1) {
         const int2 cd = a.dp.ab[Q];
-        b = quartet_bound(a, ab.x, ab.y, cd.x, cd.y, P, Q);
+        b = quartet_bound(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
       }
       const bool is32 = b >= 0.0f && b < a.fp32_cutoff_f, is64 = b >= 0.0f && !is32;
       const unsigned m64 = __ballot_sync(0xffffffffu, is64), m32 = __ballot_sync(0xffffffffu, is32);
@@ -413,7 +409,7 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
       n32 += __popc(m32);
       __syncwarp();
       if (n64 >= 32) {
-        drain_reg<LA, LB, LC, LD>(a, P, q64, 32, false, eri_col, lane);
+        drain_reg<LA, LB, LC, LD>(a, mv, P, q64, 32, false, eri_col, lane);
         __syncwarp();
         const int rest = lane + 32 < n64 ? q64[lane + 32] : 0;
         __syncwarp();
@@ -422,7 +418,7 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
         __syncwarp();
       }
       if (n32 >= 32) {
-        drain_reg<LA, LB, LC, LD>(a, P, q32, 32, true, eri_col, lane);
+        drain_reg<LA, LB, LC, LD>(a, mv, P, q32, 32, true, eri_col, lane);
         __syncwarp();
         const int rest = lane + 32 < n32 ? q32[lane + 32] : 0;
         __syncwarp();
@@ -431,8 +427,8 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
         __syncwarp();
       }
     }
-    drain_reg<LA, LB, LC, LD>(a, P, q64, n64, false, eri_col, lane);
-    drain_reg<LA, LB, LC, LD>(a, P, q32, n32, true, eri_col, lane);
+    drain_reg<LA, LB, LC, LD>(a, mv, P, q64, n64, false, eri_col, lane);
+    drain_reg<LA, LB, LC, LD>(a, mv, P, q32, n32, true, eri_col, lane);
     __syncwarp();
   }
 }
