@@ -199,6 +199,20 @@ FOCK_API fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_
  * symmetrisation); -1 for NULL.  Host only. */
 FOCK_API int32_t fock_kernels_per_build(const fock_shellpairs *sp);
 
+/*
+ * FP64 one-electron integrals for the RHF driver (Sec. 2.2: F = h + J - K/2,
+ * h = T + V): overlap S, kinetic T and nuclear attraction V over the same
+ * normalised Cartesian basis as the J/K build, by the McMurchie-Davidson
+ * Hermite expansion (Sec. 4.1) with the tabulated Boys function.
+ *   desc: host basis (as fock_shellpairs_build).  natom nuclei with charges
+ *   Z[natom] and positions xyz[3*natom] (bohr), host.
+ *   S, T, V: device, N x N row-major float64, overwritten (full, symmetric).
+ * Synchronises the stream.  Errors: FOCK_ERR_INVALID_ARG,
+ * FOCK_ERR_UNSUPPORTED_L, FOCK_ERR_OOM, FOCK_ERR_CUDA.
+ */
+FOCK_API fock_status fock_one_electron(const fock_basis_desc *desc, int32_t natom, const double *Z,
+                                       const double *xyz, double *S, double *T, double *V, cudaStream_t stream);
+
 /* Synchronise the stream, return and clear the device status word
  * (FOCK_OK if no device-side error was recorded). */
 FOCK_API fock_status fock_stream_status(cudaStream_t stream);

@@ -55,6 +55,8 @@ def lib():
             _lib.oracle_jk_blocks.argtypes = basis + [p, d, i, d, i, p, p, i, p, p]
             _lib.oracle_count.argtypes = basis + [p, d, p]
             _lib.oracle_jk_sample.argtypes = basis + [p, d, i, d, i, i, p, p, p]
+            _lib.oracle_kinetic.argtypes = basis + [p]
+            _lib.oracle_nuclear.argtypes = basis + [i, p, p, p]
     return _lib
 
 
@@ -115,6 +117,28 @@ def overlap(basis: dict) -> np.ndarray:
     if lib().oracle_overlap(*args, _ptr(S)):
         raise ValueError("bad basis")
     return S
+
+
+def kinetic(basis: dict) -> np.ndarray:
+    """Kinetic energy matrix, 1/2 sum_x <d_x a|d_x b> (Sec. 2.2 core Hamiltonian)."""
+    args, keep = _basis_args(basis)
+    n = nbf(basis)
+    T = np.zeros((n, n))
+    if lib().oracle_kinetic(*args, _ptr(T)):
+        raise ValueError("bad basis")
+    return T
+
+
+def nuclear(basis: dict, Z, xyz) -> np.ndarray:
+    """Nuclear attraction matrix -sum_C Z_C <a|1/|r-C||b> (Obara-Saika + HRR)."""
+    args, keep = _basis_args(basis)
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    n = nbf(basis)
+    V = np.zeros((n, n))
+    if lib().oracle_nuclear(*args, len(Z), _ptr(Z), _ptr(xyz), _ptr(V)):
+        raise ValueError("bad basis")
+    return V
 
 
 def shell_eri(basis: dict, a: int, b: int, c: int, d: int) -> np.ndarray:

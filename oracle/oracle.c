@@ -28,6 +28,11 @@
  *     largest contracted G_ab (primitive-level pruning, Sec. 3.2).
  *
  * Every J/K accumulation uses Neumaier-compensated sums.
+ *
+ * One-electron integrals for the SCF driver (Sec. 2.2, h = T + V): overlap
+ * and kinetic energy from one-dimensional Obara-Saika overlaps (kinetic as
+ * 1/2 sum_x <d_x a|d_x b>), nuclear attraction by the Obara-Saika
+ * nuclear-attraction vertical recurrence and the horizontal recurrence.
  */
 #include <math.h>
 #include <stdint.h>
@@ -876,5 +881,160 @@ int oracle_count(int nshell, const double *center, const int32_t *l, const int32
   out[2] = q2;
   out[3] = e2;
   or_setup_free(&S);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* one-electron integrals                                                      */
+/* ------------------------------------------------------------------------- */
+/* 1-D overlap table s[i][j], i <= imax, j <= jmax, unnormalised primitives */
+static void or_overlap1d(int imax, int jmax, double a, double b, double Ax, double Bx, double s[8][8]) {
+  double p = a + b, Px = (a * Ax + b * Bx) / p, XAB = Ax - Bx;
+  s[0][0] = sqrt(M_PI / p) * exp(-a * b / p * XAB * XAB);
+  for (int i = 0; i <= imax; ++i)
+    for (int j = 0; j <= jmax; ++j) {
+      if (i == 0 && j == 0) continue;
+      double v;
+      if (i > 0) {
+        v = (Px - Ax) * s[i - 1][j];
+        if (i > 1) v += (i - 1) * s[i - 2][j] / (2 * p);
+        if (j > 0) v += j * s[i - 1][j - 1] / (2 * p);
+      } else {
+        v = (Px - Bx) * s[i][j - 1];
+        if (j > 1) v += (j - 1) * s[i][j - 2] / (2 * p);
+      }
+      s[i][j] = v;
+    }
+}
+
+/* Kinetic energy matrix T = 1/2 sum_x <d_x a | d_x b>, normalised functions. */
+int oracle_kinetic(int nshell, const double *center, const int32_t *l, const int32_t *nprim,
+                   const int32_t *prim_off, const double *exps, const double *coefs, double *T) {
+  or_basis B = {nshell, center, l, nprim, prim_off, exps, coefs};
+  or_ctx X;
+  if (or_ctx_init(&X, &B)) return 1;
+  int N = X.nbf;
+  for (int sa = 0; sa < nshell; ++sa)
+    for (int sb = 0; sb < nshell; ++sb) {
+      int la = l[sa], lb = l[sb], na = OR_NC(la), nb = OR_NC(lb);
+      const double *A = center + 3 * sa, *Bc = center + 3 * sb;
+      int ba = OR_NH(la - 1) * (la > 0), bb = OR_NH(lb - 1) * (lb > 0);
+      for (int ia = 0; ia < na; ++ia)
+        for (int ib = 0; ib < nb; ++ib) {
+          const int *u = g_cvec[ba + ia], *v = g_cvec[bb + ib];
+          double acc = 0.0;
+          for (int i = 0; i < nprim[sa]; ++i)
+            for (int j = 0; j < nprim[sb]; ++j) {
+              double a = exps[prim_off[sa] + i], b = exps[prim_off[sb] + j];
+              double s[3][8][8];
+              for (int x = 0; x < 3; ++x) or_overlap1d(la + 1, lb + 1, a, b, A[x], Bc[x], s[x]);
+              double t = 0.0;
+              for (int x = 0; x < 3; ++x) {
+                /* d/dx of x^k exp(-a x^2) = k x^(k-1) - 2a x^(k+1) */
+                int ka = u[x], kb = v[x];
+                double d = 4.0 * a * b * s[x][ka + 1][kb + 1];
+                if (ka > 0) d -= 2.0 * b * ka * s[x][ka - 1][kb + 1];
+                if (kb > 0) d -= 2.0 * a * kb * s[x][ka + 1][kb - 1];
+                if (ka > 0 && kb > 0) d += (double)ka * kb * s[x][ka - 1][kb - 1];
+                double o = 1.0;
+                for (int y = 0; y < 3; ++y)
+                  if (y != x) o *= s[y][u[y]][v[y]];
+                t += 0.5 * d * o;
+              }
+              acc += X.coef[prim_off[sa] + i] * X.coef[prim_off[sb] + j] * t;
+            }
+          T[(size_t)(X.bf_off[sa] + ia) * N + X.bf_off[sb] + ib] =
+              acc * or_cart_norm(u[0], u[1], u[2]) * or_cart_norm(v[0], v[1], v[2]);
+        }
+    }
+  or_ctx_free(&X);
+  return 0;
+}
+
+/* Nuclear attraction V = -sum_C Z_C <a| 1/|r - C| |b>, normalised functions:
+ * Obara-Saika vertical recurrence on the bra with auxiliary orders
+ * Theta^(m)(0,0) = (2 pi / p) K_AB F_m(p |PC|^2), then the horizontal
+ * recurrence (a|b+1_i) = (a+1_i|b) + AB_i (a|b). */
+int oracle_nuclear(int nshell, const double *center, const int32_t *l, const int32_t *nprim,
+                   const int32_t *prim_off, const double *exps, const double *coefs, int natom,
+                   const double *Z, const double *xyz, double *V) {
+  or_basis B = {nshell, center, l, nprim, prim_off, exps, coefs};
+  or_ctx X;
+  if (or_ctx_init(&X, &B)) return 1;
+  int N = X.nbf;
+  double th[OR_NHE][OR_MMAX + 1];
+  double cont[OR_NHE];
+  double hr[OR_NHE][OR_NH(OR_LMAX)];
+  for (int sa = 0; sa < nshell; ++sa)
+    for (int sb = 0; sb < nshell; ++sb) {
+      int la = l[sa], lb = l[sb], L = la + lb;
+      const double *A = center + 3 * sa, *Bc = center + 3 * sb;
+      double AB[3], AB2 = 0.0;
+      for (int x = 0; x < 3; ++x) {
+        AB[x] = A[x] - Bc[x];
+        AB2 += AB[x] * AB[x];
+      }
+      for (int e = 0; e < OR_NH(L); ++e) cont[e] = 0.0;
+      for (int i = 0; i < nprim[sa]; ++i)
+        for (int j = 0; j < nprim[sb]; ++j) {
+          double a = exps[prim_off[sa] + i], b = exps[prim_off[sb] + j], p = a + b;
+          double P[3], PA[3];
+          for (int x = 0; x < 3; ++x) {
+            P[x] = (a * A[x] + b * Bc[x]) / p;
+            PA[x] = P[x] - A[x];
+          }
+          double cc = X.coef[prim_off[sa] + i] * X.coef[prim_off[sb] + j] * 2.0 * M_PI / p * exp(-a * b / p * AB2);
+          for (int c = 0; c < natom; ++c) {
+            double PC[3], PC2 = 0.0;
+            for (int x = 0; x < 3; ++x) {
+              PC[x] = P[x] - xyz[3 * c + x];
+              PC2 += PC[x] * PC[x];
+            }
+            double F[OR_MMAX + 1];
+            oracle_boys(L, p * PC2, F);
+            for (int m = 0; m <= L; ++m) th[0][m] = cc * F[m];
+            for (int ie = 1; ie < OR_NH(L); ++ie) {
+              int v[3] = {g_cvec[ie][0], g_cvec[ie][1], g_cvec[ie][2]};
+              int k = v[0] > 0 ? 0 : (v[1] > 0 ? 1 : 2);
+              v[k] -= 1;
+              int e1 = g_cidx[v[0]][v[1]][v[2]], nk = v[k], e2 = -1;
+              if (nk > 0) {
+                v[k] -= 1;
+                e2 = g_cidx[v[0]][v[1]][v[2]];
+              }
+              int deg = g_cvec[ie][0] + g_cvec[ie][1] + g_cvec[ie][2];
+              for (int m = 0; m <= L - deg; ++m) {
+                double val = PA[k] * th[e1][m] - PC[k] * th[e1][m + 1];
+                if (e2 >= 0) val += nk / (2.0 * p) * (th[e2][m] - th[e2][m + 1]);
+                th[ie][m] = val;
+              }
+            }
+            for (int e = 0; e < OR_NH(L); ++e) cont[e] -= Z[c] * th[e][0];
+          }
+        }
+      /* HRR: hr[e][b] = (e|b) for |e| in [la, la+lb-|b|] */
+      for (int e = OR_NH(la - 1) * (la > 0); e < OR_NH(L); ++e) hr[e][0] = cont[e];
+      for (int jb = 1; jb < OR_NH(lb); ++jb) {
+        int v[3] = {g_cvec[jb][0], g_cvec[jb][1], g_cvec[jb][2]};
+        int bdeg = v[0] + v[1] + v[2];
+        int k = v[0] > 0 ? 0 : (v[1] > 0 ? 1 : 2);
+        v[k] -= 1;
+        int bm = g_cidx[v[0]][v[1]][v[2]];
+        for (int e = OR_NH(la - 1) * (la > 0); e < OR_NH(L - bdeg); ++e) {
+          int av[3] = {g_cvec[e][0], g_cvec[e][1], g_cvec[e][2]};
+          av[k] += 1;
+          int ep = g_cidx[av[0]][av[1]][av[2]];
+          hr[e][jb] = hr[ep][bm] + AB[k] * hr[e][bm];
+        }
+      }
+      int ba = OR_NH(la - 1) * (la > 0), bb = OR_NH(lb - 1) * (lb > 0);
+      for (int ia = 0; ia < OR_NC(la); ++ia)
+        for (int ib = 0; ib < OR_NC(lb); ++ib) {
+          const int *u = g_cvec[ba + ia], *w = g_cvec[bb + ib];
+          V[(size_t)(X.bf_off[sa] + ia) * N + X.bf_off[sb] + ib] =
+              hr[ba + ia][bb + ib] * or_cart_norm(u[0], u[1], u[2]) * or_cart_norm(w[0], w[1], w[2]);
+        }
+    }
+  or_ctx_free(&X);
   return 0;
 }

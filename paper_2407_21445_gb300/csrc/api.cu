@@ -209,6 +209,8 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
 }  // namespace
 
 namespace fk {
+fock_status validate_basis(const fock_basis_desc *d) { return validate(d); }
+void normalised_coefs(const fock_basis_desc *d, int s, double *out) { norm_coefs(d, s, out); }
 fock_status upload_staging(const Staging &st, const std::vector<Unit> &units, void **base, DevPairs &dp,
                            Unit **d_units, size_t *bytes, cudaStream_t stream) {
   return upload(st, units, base, dp, d_units, bytes, stream);

@@ -105,6 +105,19 @@ __device__ __forceinline__ void boys_seeds(const double *__restrict__ tab, const
   }
 }
 
+// F_m(T), m = 0..L (no seed scaling), full FP64 (one-electron integrals).
+__device__ __forceinline__ void boys_eval_all(const double *__restrict__ tab, int L, double T, double *F) {
+  if (T < BOYS_TMAX) {
+    const int gi = (int)(T * BOYS_INVH + 0.5);
+    const double x = gi * BOYS_H - T;
+    for (int m = 0; m <= L; ++m) F[m] = boys_taylor(tab, gi, m, x);
+  } else {
+    F[0] = 0.88622692545275801365 * rsqrt(T);
+    const double it = 1.0 / T;
+    for (int m = 1; m <= L; ++m) F[m] = F[m - 1] * (m - 0.5) * it;
+  }
+}
+
 // Runtime-L variant for the group-cooperative kernel: lanes gl, gl+G, ...
 // write seeds m into F[]; the lane that writes m = L also writes R0[0].
 template <int G>

@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
             L.fock_work_stats.restype = i
             L.fock_stream_status.argtypes = [p]
             L.fock_stream_status.restype = i
+            L.fock_one_electron.argtypes = [ctypes.POINTER(fock_basis_desc), i, p, p, p, p, p, p]
+            L.fock_one_electron.restype = i
             L.fock_debug_bounds.argtypes = [p]
             L.fock_debug_bounds.restype = i
             L.fock_last_error.argtypes = []
@@ -203,6 +205,20 @@ def fock_work_stats(handle, D_host: np.ndarray, schwarz_thresh: float) -> dict:
 
 def fock_stream_status(stream=None) -> int:
     return int(lib().fock_stream_status(_stream_handle(stream)))
+
+
+def fock_one_electron(basis: dict, Z, xyz, stream=None):
+    """Overlap, kinetic and nuclear-attraction matrices (device float64 tensors)."""
+    import torch
+    arr = _BasisArrays(basis)
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    n = int(sum((int(l) + 1) * (int(l) + 2) // 2 for l in arr.l))
+    S, T, V = (torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(3))
+    rc = lib().fock_one_electron(ctypes.byref(arr.desc), len(Z), _np_ptr(Z), _np_ptr(xyz), _tensor_ptr(S, "S"),
+                                 _tensor_ptr(T, "T"), _tensor_ptr(V, "V"), _stream_handle(stream))
+    _check(rc, "fock_one_electron")
+    return S, T, V
 
 
 def fock_debug_bounds():

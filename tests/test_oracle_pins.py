@@ -370,3 +370,57 @@ def test_count_matches_brute_force():
                         e += np.prod([oracle.ncart(int(ls[s])) for s in (a, b, c, d)])
     cnt = oracle.count(p.basis, p.D, p.tau)
     assert cnt["quartets_schwarz"] == q and cnt["eris_schwarz"] == e
+
+
+# --------------------------------------------------------------------------
+# one-electron integrals (core Hamiltonian h = T + V, Sec. 2.2)
+# --------------------------------------------------------------------------
+
+def test_one_electron_single_gaussian_closed_forms():
+    """Normalised Gaussian r^l exp(-a r^2) on a nucleus of charge Z:
+    T = (2l+3) a / 2 and <1/r> = 2^(l+1) l! sqrt(2a) / ((2l+1)!! sqrt(pi))."""
+    C = np.array([0.3, -0.2, 0.1])
+    for a in (0.3, 2.0, 11.0):
+        for l, comp in ((0, 0), (1, 0), (1, 2)):
+            bas = molgen.single_shell_basis([(l, C, [a], [1.0])])
+            T = oracle.kinetic(bas)
+            V = oracle.nuclear(bas, [3.0], [C])
+            dfact = 1 if l == 0 else 3
+            r1 = 2 ** (l + 1) * math.factorial(l) * math.sqrt(2 * a) / (dfact * math.sqrt(math.pi))
+            assert abs(T[comp, comp] - (2 * l + 3) * a / 2) < 1e-13 * a
+            assert abs(V[comp, comp] + 3.0 * r1) < 1e-13 * r1
+
+
+def test_one_electron_two_s_closed_forms(rng):
+    """T_ab = mu (3 - 2 mu R^2) S_ab; V_ab = -Z 2pi/p K_AB N_a N_b F_0(p |PC|^2)."""
+    for _ in range(20):
+        a, b = rng.uniform(0.2, 6, 2)
+        A, B, Cn = rng.uniform(-1.5, 1.5, (3, 3))
+        bas = molgen.single_shell_basis([(0, A, [a], [1.0]), (0, B, [b], [1.0])])
+        S = oracle.overlap(bas)
+        T = oracle.kinetic(bas)
+        V = oracle.nuclear(bas, [1.7], [Cn])
+        mu, p = a * b / (a + b), a + b
+        R2 = np.sum((A - B) ** 2)
+        assert abs(T[0, 1] - mu * (3 - 2 * mu * R2) * S[0, 1]) < 1e-13
+        P = (a * A + b * B) / p
+        Tn = p * np.sum((P - Cn) ** 2)
+        F0 = 1.0 if Tn == 0 else 0.5 * math.sqrt(math.pi / Tn) * math.erf(math.sqrt(Tn))
+        Na, Nb = (2 * a / math.pi) ** 0.75, (2 * b / math.pi) ** 0.75
+        ref = -1.7 * 2 * math.pi / p * math.exp(-mu * R2) * Na * Nb * F0
+        assert abs(V[0, 1] - ref) < 1e-13 * abs(ref)
+
+
+def test_one_electron_invariances(rng):
+    bas = molgen.random_shells(rng, [0, 1, 2, 3, 1], spread=1.5)
+    Zs = np.array([1.0, 6.0, 8.0])
+    at = rng.uniform(-2, 2, (3, 3))
+    shift = rng.uniform(-4, 4, 3)
+    bas2 = dict(bas)
+    bas2["center"] = bas["center"] + shift
+    T1, T2 = oracle.kinetic(bas), oracle.kinetic(bas2)
+    V1, V2 = oracle.nuclear(bas, Zs, at), oracle.nuclear(bas2, Zs, at + shift)
+    assert np.abs(T1 - T2).max() < 1e-12 and np.abs(V1 - V2).max() < 1e-11
+    assert np.abs(T1 - T1.T).max() < 1e-12 and np.abs(V1 - V1.T).max() < 1e-11
+    # the kinetic energy operator is positive definite on independent functions
+    assert np.linalg.eigvalsh(T1).min() > 0
