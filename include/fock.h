@@ -213,6 +213,38 @@ FOCK_API int32_t fock_kernels_per_build(const fock_shellpairs *sp);
 FOCK_API fock_status fock_one_electron(const fock_basis_desc *desc, int32_t natom, const double *Z,
                                        const double *xyz, double *S, double *T, double *V, cudaStream_t stream);
 
+/*
+ * Atom-pair MLP of the learned SCF guess (no counterpart in the paper; the
+ * SCF extension).  Three dense layers nin -> nhidden -> nhidden -> nout with
+ * SiLU activations; BF16 weights, FP32 activations, FP32 accumulation; FP32
+ * master parameters with Adam.  Parameter vector layout (FP32):
+ * W1[nhidden][nin], b1[nhidden], W2[nhidden][nhidden], b2[nhidden],
+ * W3[nout][nhidden], b3[nout].  All tensors are row-major device arrays
+ * owned by the caller unless stated; the handle owns parameters, gradients,
+ * optimiser state and activation buffers for max_batch rows.
+ */
+typedef struct fock_mlp fock_mlp;
+FOCK_API fock_status fock_mlp_create(int32_t nin, int32_t nhidden, int32_t nout, int32_t max_batch, uint64_t seed,
+                                     fock_mlp **out);
+FOCK_API fock_status fock_mlp_free(fock_mlp *net);
+/* number of FP32 parameters (-1 for NULL) */
+FOCK_API int64_t fock_mlp_num_params(const fock_mlp *net);
+/* copy parameters and/or accumulated gradients to host arrays of num_params floats (either may be NULL) */
+FOCK_API fock_status fock_mlp_get_params(const fock_mlp *net, float *host_params, float *host_grads);
+FOCK_API fock_status fock_mlp_set_params(fock_mlp *net, const float *host_params);
+/* Y[B][nout] = net(X[B][nin]); B <= max_batch; device pointers */
+FOCK_API fock_status fock_mlp_forward(fock_mlp *net, const float *X, int32_t B, float *Y, cudaStream_t stream);
+/* loss = sum mask (Y - T)^2 / norm over B rows (mask may be NULL); the
+ * gradient of the loss is ADDED to the handle's gradient buffer; the loss is
+ * written to *loss_host when non-NULL (synchronises the stream). */
+FOCK_API fock_status fock_mlp_loss_backward(fock_mlp *net, const float *X, const float *T, const float *mask,
+                                            int32_t B, double norm, float *loss_host, cudaStream_t stream);
+/* Adam step with decoupled weight decay on the accumulated gradients, then
+ * zero the gradients and refresh the BF16 weights. */
+FOCK_API fock_status fock_mlp_step(fock_mlp *net, float lr, float beta1, float beta2, float eps, float weight_decay,
+                                   cudaStream_t stream);
+FOCK_API fock_status fock_mlp_zero_grad(fock_mlp *net, cudaStream_t stream);
+
 /* Synchronise the stream, return and clear the device status word
  * (FOCK_OK if no device-side error was recorded). */
 FOCK_API fock_status fock_stream_status(cudaStream_t stream);

@@ -380,6 +380,41 @@ def batch_problems(n: int = 256, seed: int = 0, kind: str = "tz", tau: float = 1
     return probs
 
 
+def _nonbonded_clash(mol: Molecule, hh_ang=1.5, cc_ang=2.4) -> bool:
+    """True if two H atoms are closer than hh_ang or two non-bonded carbons
+    (farther than a bond, 1.7 A) closer than cc_ang."""
+    x = mol.coords * BOHR_ANGSTROM
+    sym = np.array(mol.symbols)
+    d = np.linalg.norm(x[:, None] - x[None], axis=-1)
+    np.fill_diagonal(d, 1e9)
+    h = sym == "H"
+    c = sym == "C"
+    if h.sum() > 1 and d[np.ix_(h, h)].min() < hh_ang:
+        return True
+    dc = d[np.ix_(c, c)]
+    return bool(((dc > 1.7) & (dc < cc_ang)).any())
+
+
+def scf_conformations(n: int = 500, seed: int = 0) -> list:
+    """Seeded conformations for the SCF / learned-guess workload, alternating
+    C8-C16 alkanes (torsions near anti/gauche, +-15 deg, clash-rejected) and
+    (H2O)8-16 clusters."""
+    rng = np.random.Generator(np.random.PCG64(40_000 + seed))
+    out = []
+    while len(out) < n:
+        if len(out) % 2 == 0:
+            k = int(rng.integers(8, 17))
+            tors = rng.choice([math.pi, math.pi / 3, -math.pi / 3], k - 3, p=[0.6, 0.2, 0.2])
+            tors = tors + rng.normal(0, math.radians(15), k - 3)
+            mol = alkane_zigzag(k, torsions=tors)
+            if _nonbonded_clash(mol):
+                continue
+        else:
+            mol = water_chain_cluster(int(rng.integers(8, 17)), rng)
+        out.append(mol)
+    return out
+
+
 def custom_problem(mol: Molecule, kind="dz", seed=0, tau=1e-10, name="custom") -> Problem:
     basis = make_basis(mol, basis_set(kind, seed))
     return Problem(name, mol, basis, density(basis, seed), tau, dict(seed=seed))

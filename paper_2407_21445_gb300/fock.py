@@ -78,6 +78,25 @@ def lib() -> ctypes.CDLL:
             L.fock_stream_status.restype = i
             L.fock_one_electron.argtypes = [ctypes.POINTER(fock_basis_desc), i, p, p, p, p, p, p]
             L.fock_one_electron.restype = i
+            L.fock_mlp_create.argtypes = [i, i, i, i, ctypes.c_uint64, ctypes.POINTER(p)]
+            L.fock_mlp_create.restype = i
+            L.fock_mlp_free.argtypes = [p]
+            L.fock_mlp_free.restype = i
+            L.fock_mlp_num_params.argtypes = [p]
+            L.fock_mlp_num_params.restype = ctypes.c_int64
+            L.fock_mlp_get_params.argtypes = [p, p, p]
+            L.fock_mlp_get_params.restype = i
+            L.fock_mlp_set_params.argtypes = [p, p]
+            L.fock_mlp_set_params.restype = i
+            L.fock_mlp_forward.argtypes = [p, p, i, p, p]
+            L.fock_mlp_forward.restype = i
+            L.fock_mlp_loss_backward.argtypes = [p, p, p, p, i, d, p, p]
+            L.fock_mlp_loss_backward.restype = i
+            L.fock_mlp_step.argtypes = [p, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, p]
+            L.fock_mlp_step.restype = i
+            L.fock_mlp_zero_grad.argtypes = [p, p]
+            L.fock_mlp_zero_grad.restype = i
             L.fock_debug_bounds.argtypes = [p]
             L.fock_debug_bounds.restype = i
             L.fock_last_error.argtypes = []
@@ -258,6 +277,73 @@ def fock_hermite_e(la: int, lb: int, alpha: float, A, beta: float, B) -> np.ndar
     _check(lib().fock_hermite_e(int(la), int(lb), float(alpha), _np_ptr(A), float(beta), _np_ptr(B), _np_ptr(out)),
            "fock_hermite_e")
     return out
+
+
+def _f32_ptr(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class MLP:
+    """The library's atom-pair MLP (fock_mlp_*): BF16 weights, FP32 accumulation."""
+
+    def __init__(self, nin: int, nhidden: int, nout: int, max_batch: int, seed: int = 0):
+        self.nin, self.nhidden, self.nout, self.max_batch = nin, nhidden, nout, max_batch
+        h = ctypes.c_void_p()
+        _check(lib().fock_mlp_create(nin, nhidden, nout, max_batch, seed, ctypes.byref(h)), "fock_mlp_create")
+        self.handle = h
+        self.nparam = int(lib().fock_mlp_num_params(h))
+
+    def params(self):
+        p = np.zeros(self.nparam, dtype=np.float32)
+        _check(lib().fock_mlp_get_params(self.handle, _np_ptr(p), None), "fock_mlp_get_params")
+        return p
+
+    def grads(self):
+        g = np.zeros(self.nparam, dtype=np.float32)
+        _check(lib().fock_mlp_get_params(self.handle, None, _np_ptr(g)), "fock_mlp_get_params")
+        return g
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparam
+        _check(lib().fock_mlp_set_params(self.handle, _np_ptr(p)), "fock_mlp_set_params")
+
+    def forward(self, X, Y=None, stream=None):
+        import torch
+        if Y is None:
+            Y = torch.empty((X.shape[0], self.nout), dtype=torch.float32, device=X.device)
+        _check(lib().fock_mlp_forward(self.handle, _f32_ptr(X, "X"), X.shape[0], _f32_ptr(Y, "Y"),
+                                      _stream_handle(stream)), "fock_mlp_forward")
+        return Y
+
+    def loss_backward(self, X, T, mask=None, norm=None, stream=None) -> float:
+        out = np.zeros(1, dtype=np.float32)
+        norm = float(mask.sum()) if (norm is None and mask is not None) else float(norm or T.numel())
+        _check(lib().fock_mlp_loss_backward(self.handle, _f32_ptr(X, "X"), _f32_ptr(T, "T"),
+                                            None if mask is None else _f32_ptr(mask, "mask"), X.shape[0], norm,
+                                            _np_ptr(out), _stream_handle(stream)), "fock_mlp_loss_backward")
+        return float(out[0])
+
+    def step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+        _check(lib().fock_mlp_step(self.handle, lr, beta1, beta2, eps, weight_decay, _stream_handle(stream)),
+               "fock_mlp_step")
+
+    def zero_grad(self, stream=None):
+        _check(lib().fock_mlp_zero_grad(self.handle, _stream_handle(stream)), "fock_mlp_zero_grad")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().fock_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class JKBuilder:

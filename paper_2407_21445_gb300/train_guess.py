@@ -1,0 +1,109 @@
+"""The learned-guess experiment: RHF on seeded conformations (C8-C16 alkanes,
+(H2O)8-16 clusters; 6-31G(d)-shaped synthetic basis; FP64 J/K; DIIS;
+convergence 1e-8 Eh) from the SAD guess; the atom-pair MLP is trained on the
+converged densities of the training conformations with the library's
+forward/backward kernels; on the held-out conformations the SCF is rerun
+from the MLP guess and compared with SAD by iterations, time and energy.
+
+    python -m paper_2407_21445_gb300.train_guess --n 500 --train 400 --out DIR
+
+Writes DIR/report.json and DIR/mlp_params.npz (network, feature normaliser).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+import molgen
+
+from . import guess as G
+from .scf import RHF, sad_guess
+
+
+def run(n: int, ntrain: int, out: str, epochs: int, seed: int = 0, tau: float = 1e-10, log=print):
+    os.makedirs(out, exist_ok=True)
+    table = molgen.basis_set("dz", seed)
+    mols = molgen.scf_conformations(n, seed)
+    rng = np.random.Generator(np.random.PCG64(50_000 + seed))
+    order = rng.permutation(n)
+    train_idx, test_idx = sorted(order[:ntrain].tolist()), sorted(order[ntrain:].tolist())
+    rec = {}
+    feats, targs, masks = [], [], []
+    t0 = time.time()
+    for i in range(n):
+        mol = mols[i]
+        basis = molgen.make_basis(mol, table)
+        rhf = RHF(mol.Z.astype(float), mol.coords, basis, tau=tau)
+        ts = time.time()
+        r = rhf.run(sad_guess(mol, table))
+        torch.cuda.synchronize()
+        rec[i] = dict(natom=mol.natom, nbf=int(rhf.S.shape[0]), sad_E=r.energy, sad_it=r.iterations,
+                      sad_conv=r.converged, sad_t=time.time() - ts)
+        if i in set(train_idx):
+            pairs, frames, f = G.pair_frames(mol)
+            T, M = G.blocks_to_local(r.D.cpu().numpy(), mol, basis, pairs, frames)
+            feats.append(f)
+            targs.append(T)
+            masks.append(M)
+        if i % 25 == 0:
+            log(f"scf {i}/{n} nbf={rec[i]['nbf']} it={r.iterations} E={r.energy:.8f} ({time.time() - t0:.0f}s)")
+    F, T, M = np.concatenate(feats), np.concatenate(targs), np.concatenate(masks)
+    log(f"training samples {F.shape[0]}")
+    lg = G.LearnedGuess(hidden=128, max_batch=8192, seed=seed)
+    lg.fit_normaliser(F)
+    tt = time.time()
+    hist = lg.train(F, T, M, epochs=epochs, batch=4096, lr=2e-3, seed=seed, log=log)
+    train_s = time.time() - tt
+    res = []
+    for i in test_idx:
+        mol = mols[i]
+        basis = molgen.make_basis(mol, table)
+        rhf = RHF(mol.Z.astype(float), mol.coords, basis, tau=tau)
+        ts = time.time()
+        D0 = lg.guess(mol, basis, rhf)
+        r = rhf.run(D0)
+        torch.cuda.synchronize()
+        rr = dict(rec[i])
+        rr.update(mlp_E=r.energy, mlp_it=r.iterations, mlp_conv=r.converged, mlp_t=time.time() - ts,
+                  dE=abs(r.energy - rec[i]["sad_E"]))
+        res.append(rr)
+    sad_it = np.array([r["sad_it"] for r in res], float)
+    mlp_it = np.array([r["mlp_it"] for r in res], float)
+    report = {
+        "conformations": n, "train": ntrain, "held_out": len(test_idx), "basis": "6-31G(d)-shaped synthetic",
+        "convergence": "|dE| < 1e-8 Eh and max |X^T (FDS - SDF) X| < 1e-6",
+        "held_out_mean_iterations": {"sad": float(sad_it.mean()), "mlp": float(mlp_it.mean())},
+        "iteration_reduction": float(1.0 - mlp_it.mean() / sad_it.mean()),
+        "held_out_mean_time_s": {"sad": float(np.mean([r["sad_t"] for r in res])),
+                                 "mlp": float(np.mean([r["mlp_t"] for r in res]))},
+        "max_abs_energy_diff_Eh": float(max(r["dE"] for r in res)),
+        "all_converged": bool(all(r["sad_conv"] and r["mlp_conv"] for r in res)),
+        "train_mean_sad_iterations": float(np.mean([rec[i]["sad_it"] for i in train_idx])),
+        "training_loss_first_last": [float(hist[0]), float(hist[-1])], "training_seconds": train_s,
+        "epochs": epochs, "samples": int(F.shape[0]), "per_molecule": res,
+    }
+    with open(os.path.join(out, "report.json"), "w") as f:
+        json.dump(report, f, indent=1)
+    np.savez(os.path.join(out, "mlp_params.npz"), params=lg.net.params(), mu=lg.mu, sd=lg.sd)
+    return report
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=500)
+    ap.add_argument("--train", type=int, default=400)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default="guess_run")
+    a = ap.parse_args()
+    rep = run(a.n, a.train, a.out, a.epochs, a.seed)
+    print(json.dumps({k: v for k, v in rep.items() if k != "per_molecule"}))
+
+
+if __name__ == "__main__":
+    main()

@@ -424,3 +424,36 @@ def test_one_electron_invariances(rng):
     assert np.abs(T1 - T1.T).max() < 1e-12 and np.abs(V1 - V1.T).max() < 1e-11
     # the kinetic energy operator is positive definite on independent functions
     assert np.linalg.eigvalsh(T1).min() > 0
+
+
+# --------------------------------------------------------------------------
+# reference MLP of the learned guess: analytic gradient vs finite differences
+# --------------------------------------------------------------------------
+
+def test_mlp_reference_gradient_finite_differences(rng):
+    from oracle import mlp_ref
+    nin, H, nout, B = 7, 9, 5, 11
+    n = H * nin + H + H * H + H + nout * H + nout
+    p = rng.normal(0, 0.4, n)
+    X = rng.normal(0, 1, (B, nin))
+    T = rng.normal(0, 1, (B, nout))
+    mask = (rng.uniform(0, 1, (B, nout)) > 0.3).astype(float)
+    loss, g = mlp_ref.loss_and_grad(p, X, T, mask, mask.sum(), nin, H, nout, weights_bf16=False)
+    for k in rng.choice(n, 25, replace=False):
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        lp, _ = mlp_ref.loss_and_grad(pp, X, T, mask, mask.sum(), nin, H, nout, weights_bf16=False)
+        lm, _ = mlp_ref.loss_and_grad(pm, X, T, mask, mask.sum(), nin, H, nout, weights_bf16=False)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-7 * max(1.0, abs(g[k])), (k, fd, g[k])
+
+
+def test_bf16_rounding_reference():
+    from oracle import mlp_ref
+    x = np.array([1.0, 1.00390625, 1.005859375, -3.14159, 65504.0, 1e-3], dtype=np.float32)
+    r = mlp_ref.bf16_round(x)
+    # bfloat16 keeps 8 significant bits: relative rounding error <= 2^-9
+    assert np.all(np.abs(r - x) <= np.abs(x) * 2.0 ** -8)
+    assert r[0] == 1.0 and r[1] == 1.0  # 1 + 2^-8 is a tie that rounds to even
