@@ -1,7 +1,9 @@
 """Learned initial density for the RHF driver: an atom-pair MLP (the library's
-fock_mlp kernels) predicts every atom-pair block of the density matrix in a
-local frame of the pair; the blocks are rotated back, assembled and projected
-onto an idempotent density (natural orbitals of D S, the nocc largest kept).
+fock_mlp kernels) predicts, for every atom pair, the correction from the
+superposition-of-atomic-densities (SAD) block to the converged density block
+in a local frame of the pair; the blocks are rotated back, added to the SAD
+density and projected onto an idempotent density (natural orbitals of D S,
+the nocc largest kept).
 
 Host-side input preparation only (frames, features, block rotations); the
 network's forward and backward passes run in the library's CUDA kernels.
@@ -18,7 +20,7 @@ from .fock import MLP
 ELEM = {"H": 0, "C": 1, "O": 2}
 MAXB = 15           # functions per atom in the 6-31G(d)-shaped basis (heavy atoms)
 NOUT = MAXB * MAXB  # flattened block
-NNB = 8             # neighbours described in the pair frame
+NNB = 12            # neighbours described in the pair frame
 RBF = np.arange(0.0, 12.0, 1.0)
 NFEAT = 3 + 3 + 1 + 1 + len(RBF) + NNB * 7
 PAIR_CUTOFF = 10.0  # bohr; farther blocks are predicted as zero
@@ -230,9 +232,11 @@ class LearnedGuess:
             out.append(self.net.forward(X[i:i + self.max_batch].contiguous()).cpu().numpy())
         return np.concatenate(out) if out else np.zeros((0, NOUT), dtype=np.float32)
 
-    def guess(self, mol, basis, rhf) -> torch.Tensor:
+    def guess(self, mol, basis, rhf, D_sad: np.ndarray) -> torch.Tensor:
+        """SAD density plus the predicted correction, projected to an
+        idempotent closed-shell density."""
         pairs, frames, feats = pair_frames(mol)
         Y = self.predict_local(feats)
-        D = local_to_density(Y, mol, basis, pairs, frames, rhf.S.shape[0])
+        D = D_sad + local_to_density(Y, mol, basis, pairs, frames, rhf.S.shape[0])
         Dt = torch.tensor(D, device=rhf.S.device, dtype=rhf.S.dtype)
         return project_idempotent(Dt, rhf.S, rhf.X, rhf.nocc)

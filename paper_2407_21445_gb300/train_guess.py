@@ -40,13 +40,14 @@ def run(n: int, ntrain: int, out: str, epochs: int, seed: int = 0, tau: float = 
         basis = molgen.make_basis(mol, table)
         rhf = RHF(mol.Z.astype(float), mol.coords, basis, tau=tau)
         ts = time.time()
-        r = rhf.run(sad_guess(mol, table))
+        Ds = sad_guess(mol, table)
+        r = rhf.run(Ds)
         torch.cuda.synchronize()
         rec[i] = dict(natom=mol.natom, nbf=int(rhf.S.shape[0]), sad_E=r.energy, sad_it=r.iterations,
                       sad_conv=r.converged, sad_t=time.time() - ts)
         if i in set(train_idx):
             pairs, frames, f = G.pair_frames(mol)
-            T, M = G.blocks_to_local(r.D.cpu().numpy(), mol, basis, pairs, frames)
+            T, M = G.blocks_to_local(r.D.cpu().numpy() - Ds.cpu().numpy(), mol, basis, pairs, frames)
             feats.append(f)
             targs.append(T)
             masks.append(M)
@@ -65,7 +66,7 @@ def run(n: int, ntrain: int, out: str, epochs: int, seed: int = 0, tau: float = 
         basis = molgen.make_basis(mol, table)
         rhf = RHF(mol.Z.astype(float), mol.coords, basis, tau=tau)
         ts = time.time()
-        D0 = lg.guess(mol, basis, rhf)
+        D0 = lg.guess(mol, basis, rhf, sad_guess(mol, table).cpu().numpy())
         r = rhf.run(D0)
         torch.cuda.synchronize()
         rr = dict(rec[i])
@@ -97,7 +98,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=500)
     ap.add_argument("--train", type=int, default=400)
-    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default="guess_run")
     a = ap.parse_args()
