@@ -72,6 +72,9 @@ typedef struct {
   const int32_t *atom;
 } fock_basis_desc;
 
+/* Angular-momentum classes of a shell pair, ss .. ff (l <= 3). */
+#define FOCK_NCLASS 10
+
 /* Options; pass NULL for the defaults shown. */
 typedef struct {
   int32_t precision;    /* FOCK_FP64 (default) or FOCK_MIXED                     */
@@ -87,8 +90,25 @@ typedef struct {
   int32_t reg_max_L;      /* class pairs with total angular momentum up to this
                              use the per-class register kernels (0 = default 4;
                              -1 = none)                                          */
-  int32_t reserved[5];
+  int32_t tune_isolate;   /* 1: every class pair gets launches of its own, so
+                             that its time can be measured (fock_autotune);
+                             0 (default): class pairs with the same kernel
+                             share one launch                                  */
+  int8_t schedule[FOCK_NCLASS * FOCK_NCLASS];
+                          /* per class pair {x, y}, entry [min(x,y) * FOCK_NCLASS
+                             + max(x,y)] (class index of shell pair (la >= lb):
+                             la (la + 1) / 2 + lb, ss = 0 ... ff = 9):
+                             0 = the built-in rule; -1 = the per-class register
+                             kernel where one exists for the pair (else the
+                             built-in rule); 1, 2, 4, 8, 16, 32 = the group
+                             kernel with that many lanes per quartet (raised
+                             where a warp's scratch would not fit).  Filled by
+                             fock_autotune.  Ignored where group_override > 0. */
+  int8_t reserved[4];
 } fock_opts;
+
+/* sizeof(fock_opts) as compiled into the library (binding layout check). */
+FOCK_API int32_t fock_opts_size(void);
 
 typedef struct fock_shellpairs fock_shellpairs; /* opaque, library-owned */
 
@@ -198,6 +218,35 @@ FOCK_API fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_
  * preparation, one persistent ERI/digestion kernel per work tier, the final
  * symmetrisation); -1 for NULL.  Host only. */
 FOCK_API int32_t fock_kernels_per_build(const fock_shellpairs *sp);
+
+/*
+ * Measured per-class-pair schedule (no counterpart in the paper, whose kernels
+ * use fixed block sizes of 64 or 128 threads per class, Sec. 4.2).  For each
+ * candidate schedule (the register kernel, group kernels of 1, 2, 4, 8, 16, 32
+ * lanes per quartet) the workload is planned with tune_isolate = 1 and built
+ * `reps` times with CUDA events around every launch; each class pair present
+ * then takes the candidate with the smallest time if it beats the built-in
+ * rule by more than 3%.  Finally the whole build is timed with the base and
+ * the tuned schedule (tune_isolate = 0, `reps` builds each, median) and the
+ * faster of the two is returned.
+ *   descs[nmol], D[nmol]: the workload (host basis descriptions as
+ *   fock_shellpairs_build; device N_i x N_i row-major float64 densities).
+ *   nmol == 1 times fock_build_jk, nmol > 1 times fock_build_jk_batched
+ *   (the batched path without its graph while measuring class pairs).
+ *   base: starting options (NULL = defaults); its schedule entries other
+ *   than 0 are kept where no candidate beats them.  schwarz_thresh as for
+ *   fock_shellpairs_build and fock_build_jk.  reps in 1..100.
+ *   *tuned: receives base with the chosen schedule (tune_isolate = 0).
+ *   ms[0], ms[1] (may be NULL): median build time in milliseconds with the
+ *   base and with the tuned schedule; *tuned is the faster of the two.
+ * Allocates and frees its own J, K and handles; synchronises `stream`;
+ * takes seconds (7 candidate plans, (reps + 1) builds each).
+ * Errors: as fock_shellpairs_build and fock_build_jk; FOCK_ERR_INVALID_ARG
+ * for null pointers, nmol < 1 or reps outside 1..100.
+ */
+FOCK_API fock_status fock_autotune(const fock_basis_desc *const *descs, int32_t nmol, const double *const *D,
+                                   const fock_opts *base, double schwarz_thresh, int32_t reps,
+                                   cudaStream_t stream, fock_opts *tuned, double *ms);
 
 /*
  * FP64 one-electron integrals for the RHF driver (Sec. 2.2: F = h + J - K/2,

@@ -281,6 +281,33 @@ int32_t fock_kernels_per_build(const fock_shellpairs *sp) {
   return n;
 }
 
+extern "C++" {
+namespace fk {
+fock_opts default_opts() {
+  fock_opts o{};
+  o.precision = FOCK_FP64;
+  o.fp32_cutoff = 1e-5;
+  o.prune_eps = 1e-3;
+  return o;
+}
+
+bool valid_opts(const fock_opts &o) {
+  if (o.precision != FOCK_FP64 && o.precision != FOCK_MIXED) return false;
+  if (!(o.prune_eps >= 0.0) || o.group_override < 0 || o.group_override > 32 || o.warp_scratch < 0 ||
+      (o.group_override & (o.group_override - 1)) != 0)
+    return false;
+  if (o.tune_isolate != 0 && o.tune_isolate != 1) return false;
+  for (int i = 0; i < FOCK_NCLASS * FOCK_NCLASS; ++i) {
+    const int v = o.schedule[i];
+    if (!(v == -1 || v == 0 || v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32)) return false;
+  }
+  return true;
+}
+}  // namespace fk
+}  // extern "C++"
+
+int32_t fock_opts_size(void) { return (int32_t)sizeof(fock_opts); }
+
 fock_status fock_shellpairs_free(fock_shellpairs *sp) {
   if (!sp) return FOCK_OK;
   if (sp->d_block) cudaFree(sp->d_block);
@@ -295,16 +322,8 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
   fock_status vs = validate(desc);
   if (vs != FOCK_OK) return vs;
   if (!(schwarz_thresh > 0.0) || !isfinite(schwarz_thresh)) return FOCK_ERR_INVALID_ARG;
-  fock_opts o{};
-  o.precision = FOCK_FP64;
-  o.fp32_cutoff = 1e-5;
-  o.prune_eps = 1e-3;
-  o.group_override = 0;
-  if (opts) o = *opts;
-  if (o.precision != FOCK_FP64 && o.precision != FOCK_MIXED) return FOCK_ERR_INVALID_ARG;
-  if (!(o.prune_eps >= 0.0) || o.group_override < 0 || o.group_override > 32 || o.warp_scratch < 0 ||
-      (o.group_override & (o.group_override - 1)) != 0)
-    return FOCK_ERR_INVALID_ARG;
+  const fock_opts o = opts ? *opts : default_opts();
+  if (!valid_opts(o)) return FOCK_ERR_INVALID_ARG;
 
   cudaError_t ce = upload_tables(stream);
   if (ce != cudaSuccess) return to_status(ce);
@@ -468,6 +487,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     double cost;   // per quartet estimate
     int G, scratch;
     bool reg;      // served by a per-class register kernel
+    int tag;       // class pair + 1 when every class pair is launched apart
   };
   std::vector<Task> tasks;
   for (int x = 0; x < (int)bins.size(); ++x)
@@ -496,18 +516,28 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
       class_l(bins[t.bra].cls, la, lb);
       class_l(bins[t.ket].cls, lc, ld);
       t.scratch = scratch_doubles(la, lb, lc, ld);
+      const int c1 = std::min(X.cls, Y.cls), c2 = std::max(X.cls, Y.cls);
+      const int sched = o.group_override > 0 ? 0 : o.schedule[c1 * FOCK_NCLASS + c2];
+      t.tag = o.tune_isolate ? c1 * FOCK_NCLASS + c2 + 1 : 0;
       const int budget = o.warp_scratch > 0 ? o.warp_scratch : 1536;
       int G = 1;
       while (G < 32 && (32 / G) * t.scratch > budget) G *= 2;
-      if (o.group_override > 0) {  // forced group size, raised where one warp's scratch would not fit
-        G = o.group_override;
+      const int forced = o.group_override > 0 ? o.group_override : (sched > 0 ? sched : 0);
+      if (forced > 0) {  // forced group size, raised where one warp's scratch would not fit
+        G = forced;
         while (G < 32 && (32 / G) * t.scratch > 24000) G *= 2;
       }
       t.G = G;
       {
         const int reg_max = o.reg_max_L == 0 ? 4 : o.reg_max_L;
         const int Ltot = lxa + lxb + lya + lyb;
-        t.reg = o.group_override == 0 && Ltot <= reg_max && reg_class_pair(bins[t.bra].cls, bins[t.ket].cls);
+        const bool avail = reg_class_pair(bins[t.bra].cls, bins[t.ket].cls);
+        if (sched == -1)
+          t.reg = avail;
+        else if (sched > 0)
+          t.reg = false;
+        else
+          t.reg = o.group_override == 0 && Ltot <= reg_max && avail;
       }
       tasks.push_back(t);
     }
@@ -516,19 +546,23 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
   // tiers keyed by (G, scratch bucket)
   struct TierKey {
     int G, sb, cb, ck;  // cb >= 0: register kernel of (bra class, ket class)
+    int tag;
     bool operator<(const TierKey &o2) const {
+      if (tag != o2.tag) return tag < o2.tag;
       if (cb != o2.cb) return cb < o2.cb;
       if (ck != o2.ck) return ck < o2.ck;
       return G != o2.G ? G < o2.G : sb < o2.sb;
     }
-    bool operator==(const TierKey &o2) const { return G == o2.G && sb == o2.sb && cb == o2.cb && ck == o2.ck; }
+    bool operator==(const TierKey &o2) const {
+      return G == o2.G && sb == o2.sb && cb == o2.cb && ck == o2.ck && tag == o2.tag;
+    }
   };
   auto key_of = [&bins](const Task &t) {
-    if (t.reg) return TierKey{1, 0, bins[t.bra].cls, bins[t.ket].cls};
+    if (t.reg) return TierKey{1, 0, bins[t.bra].cls, bins[t.ket].cls, t.tag};
     int sb = 0;
     while ((1 << sb) < t.scratch) ++sb;
     if (t.G < 32) sb = 0;  // one tier per G below a full warp
-    return TierKey{t.G, sb, -1, -1};
+    return TierKey{t.G, sb, -1, -1, t.tag};
   };
   std::vector<TierKey> keys;
   for (const Task &t : tasks) {
@@ -544,6 +578,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     tier.reg_cb = keys[ki].cb;
     tier.reg_ck = keys[ki].ck;
     tier.sb = keys[ki].sb;
+    tier.tag = keys[ki].tag;
     int stride = 1;
     const int chunk = (32 / tier.G) * 8;
     const size_t first = all_units.size();
@@ -613,8 +648,12 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
   return FOCK_OK;
 }
 
-fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double schwarz_thresh, double *J, double *K,
-                          cudaStream_t stream) {
+extern "C++" {
+namespace fk {
+// fock_build_jk with, when ev is given (tiers + 1 events), an event recorded
+// before every tier launch and one after the last.
+fock_status build_jk_events(const fock_shellpairs *sp, const double *D, double schwarz_thresh, double *J,
+                            double *K, cudaStream_t stream, const cudaEvent_t *ev) {
   if (!sp || !D || !J || !K) return FOCK_ERR_INVALID_ARG;
   if (!(schwarz_thresh >= sp->tau_build) || !isfinite(schwarz_thresh)) return FOCK_ERR_INVALID_ARG;
   const int ns = sp->nshell, n = sp->nbf;
@@ -646,10 +685,13 @@ fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double sch
   for (size_t t = 0; t < nt && e == cudaSuccess; ++t) {
     snprintf(tier_name, sizeof(tier_name), "k_jk tier %zu (G=%d, smem=%zu)", t, sp->tiers[t].G, sp->tiers[t].smem);
     where = tier_name;
-    e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, J, K, counters + t, stream, Df,
-                       sp->opts.fp32_cutoff, Dshf);
+    if (ev) e = cudaEventRecord(ev[t], stream);
+    if (e == cudaSuccess)
+      e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, J, K, counters + t, stream, Df,
+                         sp->opts.fp32_cutoff, Dshf);
     if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
   }
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[nt], stream);
   if (e == cudaSuccess) {
     where = "k_symmetrize";
     e = launch_symmetrize(J, K, n, stream);
@@ -661,6 +703,13 @@ fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double sch
     where = "cudaFreeAsync";
   }
   return to_status(e, where);
+}
+}  // namespace fk
+}  // extern "C++"
+
+fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double schwarz_thresh, double *J, double *K,
+                          cudaStream_t stream) {
+  return build_jk_events(sp, D, schwarz_thresh, J, K, stream, nullptr);
 }
 
 fock_status fock_stream_status(cudaStream_t stream) {
@@ -688,7 +737,6 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
   const bool mixed = sp->opts.precision == FOCK_MIXED && sp->opts.fp32_cutoff > 0.0;
   for (size_t ui = 0; ui < sp->h_units.size(); ++ui) {
     const Unit &u = sp->h_units[ui];
-    const bool reg = sp->tiers[sp->h_unit_tier[ui]].reg_cb >= 0;
     const int P = u.bra;
     const int2 ab = sp->h_ab[P];
     for (int Q = u.k0; Q < u.k1; ++Q) {
@@ -714,7 +762,7 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
       const double f = np * ft.prim[sp->h_cls[P]][sp->h_cls[Q]] + sp->h_prim[P].y * ft.bra[sp->h_cls[P]][sp->h_cls[Q]] +
                        12.0 * ne;
       fl += f;
-      if (mixed && reg && g * dm < sp->opts.fp32_cutoff) {
+      if (mixed && g * dm < sp->opts.fp32_cutoff) {
         q32 += 1;
         fl32 += f;
       }

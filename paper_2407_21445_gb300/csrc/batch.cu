@@ -77,7 +77,8 @@ bool same_opts(const fock_shellpairs *a, const fock_shellpairs *b) {
   return a->tau_build == b->tau_build && a->opts.precision == b->opts.precision &&
          a->opts.fp32_cutoff == b->opts.fp32_cutoff && a->opts.prune_eps == b->opts.prune_eps &&
          a->opts.group_override == b->opts.group_override && a->opts.warp_scratch == b->opts.warp_scratch &&
-         a->opts.reg_max_L == b->opts.reg_max_L && a->device == b->device;
+         a->opts.reg_max_L == b->opts.reg_max_L && a->opts.tune_isolate == b->opts.tune_isolate &&
+         memcmp(a->opts.schedule, b->opts.schedule, sizeof(a->opts.schedule)) == 0 && a->device == b->device;
 }
 
 fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan **out) {
@@ -88,8 +89,9 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
   bp->cutoff = bases[0]->opts.fp32_cutoff;
   Staging m;
   struct Key {
-    int cb, ck, G, sb;
+    int cb, ck, G, sb, tag;
     bool operator<(const Key &o) const {
+      if (tag != o.tag) return tag < o.tag;
       if (cb != o.cb) return cb < o.cb;
       if (ck != o.ck) return ck < o.ck;
       if (G != o.G) return G < o.G;
@@ -132,7 +134,7 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
     m.Ef.insert(m.Ef.end(), h.Ef.begin(), h.Ef.end());
     for (size_t u = 0; u < sp->h_units.size(); ++u) {
       const Tier &t = sp->tiers[sp->h_unit_tier[u]];
-      const Key k{t.reg_cb, t.reg_ck, t.reg_cb >= 0 ? 0 : t.G, t.reg_cb >= 0 ? 0 : t.sb};
+      const Key k{t.reg_cb, t.reg_ck, t.reg_cb >= 0 ? 0 : t.G, t.reg_cb >= 0 ? 0 : t.sb, t.tag};
       auto it = tier_of.find(k);
       int ti;
       if (it == tier_of.end()) {
@@ -245,7 +247,8 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
   return FOCK_OK;
 }
 
-cudaError_t enqueue(BatchPlan *bp, double tau) {
+// ev (optional, tiers + 1 events): recorded before every tier and after the last.
+cudaError_t enqueue(BatchPlan *bp, double tau, const cudaEvent_t *ev = nullptr) {
   cudaStream_t st = bp->st;
   cudaError_t e = cudaMemcpyAsync(bp->d_mt, bp->h_mt, sizeof(MolEntry) * bp->nmol, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(bp->counters, 0, sizeof(int) * (bp->tiers.size() + 1), st);
@@ -253,14 +256,67 @@ cudaError_t enqueue(BatchPlan *bp, double tau) {
   if (e == cudaSuccess)
     e = launch_dprep_batch(bp->d_mt, bp->d_dshp, bp->nmol, bp->dsh_total, bp->dev.sbf, bp->dev.sl, bp->Dsh,
                            bp->Dshf, st);
-  for (size_t t = 0; t < bp->tiers.size() && e == cudaSuccess; ++t)
-    e = launch_jk_tier_batch(bp->tiers[t], bp->dev, bp->d_mt, bp->Dsh, bp->Dshf, tau, bp->counters + t, st,
-                             bp->mixed ? bp->cutoff : 0.0);
+  for (size_t t = 0; t < bp->tiers.size() && e == cudaSuccess; ++t) {
+    if (ev) e = cudaEventRecord(ev[t], st);
+    if (e == cudaSuccess)
+      e = launch_jk_tier_batch(bp->tiers[t], bp->dev, bp->d_mt, bp->Dsh, bp->Dshf, tau, bp->counters + t, st,
+                               bp->mixed ? bp->cutoff : 0.0);
+  }
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[bp->tiers.size()], st);
   if (e == cudaSuccess) e = launch_symmetrize_batch(bp->d_mt, bp->d_n2p, bp->nmol, bp->n2_total, st);
   return e;
 }
 
 }  // namespace
+
+namespace fk {
+// The batched build of `bases` run `reps` times from a fresh merged plan,
+// without a graph, with events around every tier: ms_by_tag[tag] receives,
+// per tier tag, the smallest over the runs of the summed tier times
+// (class-pair timing for fock_autotune).  Synchronous.
+fock_status batch_tier_times(const fock_shellpairs *const *bases, int nmol, const double *const *D, double tau,
+                             double *const *J, double *const *K, int reps, cudaStream_t stream,
+                             std::vector<double> &ms_by_tag) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  BatchPlan *bp = nullptr;
+  fock_status s = build_plan(bases, nmol, &bp);
+  if (s != FOCK_OK) return s;
+  const size_t nt = bp->tiers.size();
+  std::vector<cudaEvent_t> ev(nt + 1, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i <= nt && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+  for (int i = 0; i < nmol; ++i) {
+    MolEntry m = bp->stat[i];
+    m.D = D[i];
+    m.J = J[i];
+    m.K = K[i];
+    m.Df = bp->mixed ? bp->Df + m.n2_off : nullptr;
+    bp->h_mt[i] = m;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  std::vector<double> best;
+  for (int r = 0; r <= reps && e == cudaSuccess; ++r) {  // run 0 warms up
+    e = enqueue(bp, tau, ev.data());
+    if (e == cudaSuccess) e = cudaStreamSynchronize(bp->st);
+    if (e != cudaSuccess || r == 0) continue;
+    std::vector<double> cur(ms_by_tag.size(), 0.0);
+    for (size_t t = 0; t < nt && e == cudaSuccess; ++t) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[t], ev[t + 1]);
+      const int tag = bp->tiers[t].tag;
+      if (tag >= 0 && tag < (int)cur.size()) cur[tag] += ms;
+    }
+    if (best.empty()) best = cur;
+    for (size_t i = 0; i < cur.size(); ++i) best[i] = std::min(best[i], cur[i]);
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  delete bp;
+  if (e != cudaSuccess) return cuda_status(e);
+  for (size_t i = 0; i < best.size(); ++i) ms_by_tag[i] = best[i];
+  return FOCK_OK;
+}
+}  // namespace fk
 
 extern "C" fock_status fock_build_jk_batched(const fock_shellpairs *const *bases, int32_t nmol,
                                              const double *const *D, double schwarz_thresh, double *const *J,

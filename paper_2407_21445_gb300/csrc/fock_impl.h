@@ -132,6 +132,7 @@ struct Tier {
   int reg_cb = -1;      // >= 0: per-class register kernel for (bra class, ket class)
   int reg_ck = -1;
   int sb = 0;           // scratch bucket of a full-warp group tier
+  int tag = 0;          // class pair + 1 when class pairs are launched apart (tuning)
   int G;                // lanes per quartet (group kernel)
   int stride;           // scratch doubles per group
   int warps_per_block;

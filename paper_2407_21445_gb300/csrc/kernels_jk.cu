@@ -69,51 +69,84 @@ __device__ __forceinline__ void group_sync(unsigned mask, int G) {
 // R^{(0)}_{tuv}, t+u+v <= L, into the returned buffer (one of R0/R1).
 // F must hold base values pref (-2alpha)^n F_n(T), n = 0..L; R0[0] = F[L].
 __constant__ double c_small[16] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15};
+__constant__ float c_smallf[16] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15};
 
-template <int G>
-__device__ __forceinline__ double *hermite_r(const ClassTables &ct, int L, double X, double Y, double Z,
-                                             const double *F, double *R0, double *R1, int gl,
-                                             unsigned gmask) {
-  double *cur = R0, *nxt = R1;
+template <class Real>
+__device__ __forceinline__ Real small_int(int i) {
+  if constexpr (sizeof(Real) == 8)
+    return c_small[i];
+  else
+    return c_smallf[i];
+}
+
+template <int G, class Real>
+__device__ __forceinline__ Real *hermite_r(const ClassTables &ct, int L, Real X, Real Y, Real Z, const Real *F,
+                                           Real *R0, Real *R1, int gl, unsigned gmask) {
+  Real *cur = R0, *nxt = R1;
   for (int n = L - 1; n >= 0; --n) {
     int cnt = nherm(L - n);
     for (int e = gl; e < cnt; e += G) {
-      double v;
+      Real v;
       if (e == 0) {
         v = F[n];
       } else {
         int t = ct.hvec[e][0], u = ct.hvec[e][1], w = ct.hvec[e][2];
         if (t > 0) {
           v = X * cur[hidx(t - 1, u, w)];
-          if (t > 1) v = fma(c_small[t - 1], cur[hidx(t - 2, u, w)], v);
+          if (t > 1) v = fma(small_int<Real>(t - 1), cur[hidx(t - 2, u, w)], v);
         } else if (u > 0) {
           v = Y * cur[hidx(t, u - 1, w)];
-          if (u > 1) v = fma(c_small[u - 1], cur[hidx(t, u - 2, w)], v);
+          if (u > 1) v = fma(small_int<Real>(u - 1), cur[hidx(t, u - 2, w)], v);
         } else {
           v = Z * cur[hidx(t, u, w - 1)];
-          if (w > 1) v = fma(c_small[w - 1], cur[hidx(t, u, w - 2)], v);
+          if (w > 1) v = fma(small_int<Real>(w - 1), cur[hidx(t, u, w - 2)], v);
         }
       }
       nxt[e] = v;
     }
     group_sync(gmask, G);
-    double *tmp = cur;
+    Real *tmp = cur;
     cur = nxt;
     nxt = tmp;
   }
   return cur;
 }
 
+// FP32 seeds for the group kernel (lanes over m), R0[0] = F[L].
 template <int G>
-__device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int P, int Q, int gl,
-                        unsigned gmask) {
+__device__ __forceinline__ void boys_seeds_rt_f32(const float *__restrict__ tab, float T, float pref, float m2a, int L,
+                                                  float *F, float *R0, int gl) {
+  for (int m = gl; m <= L; m += G) {
+    float f;
+    if (T < (float)BOYS_TMAX) {
+      const int gi = __float2int_rn(T * (float)BOYS_INVH);
+      const float x = (float)gi * (float)BOYS_H - T;
+      const float *c = tab + ((size_t)gi * (LTOT + 1) + m) * BOYS_TAYLOR;
+      f = __ldg(c + 5);
+      for (int k = 4; k >= 0; --k) f = fmaf(f, x, __ldg(c + k));
+    } else {
+      const float rt = rsqrtf(T), it = rt * rt;
+      f = 0.886226925452758f * rt;
+      for (int k = 1; k <= m; ++k) f *= ((float)k - 0.5f) * it;
+    }
+    float c = pref;
+    for (int k = 0; k < m; ++k) c *= m2a;
+    F[m] = f * c;
+    if (m == L) R0[0] = F[m];
+  }
+}
+
+// One contracted quartet on a group of G lanes, in FP64 (Real = double) or
+// in FP32 (Real = float, the mixed-precision path below the cutoff: FP32
+// table, pair-relative centres, FP32 copies of U, E and D, exact FP32->FP64
+// conversion of every digested element before the FP64 atomic add).
+template <int G, class Real>
+__device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_d, int P, int Q, int gl,
+                             unsigned gmask, const MolView &mv) {
+  constexpr bool F32 = sizeof(Real) == 4;
   const DevPairs &dp = a.dp;
   const int2 ab = dp.ab[P], cd = dp.ab[Q];
   const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
-  // density-weighted Schwarz screening over the six shell blocks (Sec. 3.2)
-  const MolView mv = mol_view(a, sA);
-  if (screened(a, mv, sA, sB, sC, sD, P, Q)) return;
-
   const int cb = dp.cls[P], ck = dp.cls[Q];
   const int la = dp.sl[sA], lb = dp.sl[sB], lc = dp.sl[sC], ld = dp.sl[sD];
   const int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
@@ -126,30 +159,55 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
   FK_CHECK(dp.prim[Q].x >= 0 && dp.prim[Q].x + dp.prim[Q].y <= a.nprimtot, 4, dp.prim[Q].x);
   FK_CHECK(dp.eoff[dp.prim[P].x + dp.prim[P].y - 1] + ct.nE[cb] <= a.nEtot, 5, cb);
   FK_CHECK(dp.eoff[dp.prim[Q].x + dp.prim[Q].y - 1] + ct.nE[ck] <= a.nEtot, 6, ck);
-  FK_CHECK(dp.sbf[sA] + na <= dp.nbf && dp.sbf[sB] + nb <= dp.nbf && dp.sbf[sC] + nc <= dp.nbf &&
-               dp.sbf[sD] + nd <= dp.nbf, 7, sA);
+  FK_CHECK(dp.sbf[sA] + na <= mv.N && dp.sbf[sB] + nb <= mv.N && dp.sbf[sC] + nc <= mv.N &&
+               dp.sbf[sD] + nd <= mv.N, 7, sA);
   FK_CHECK(L <= LTOT && nab <= MAXCP && ncd <= MAXCP, 8, L);
-  double *eri = scr;
-  double *Yh = eri + nab * ncd;
-  double *R0 = Yh + nhab * ncd;
-  double *R1 = R0 + nhL;
-  double *F = R1 + nhL;
+  Real *scr = reinterpret_cast<Real *>(scr_d);
+  Real *eri = scr;
+  Real *Yh = eri + nab * ncd;
+  Real *R0 = Yh + nhab * ncd;
+  Real *R1 = R0 + nhL;
+  Real *F = R1 + nhL;
+  const Real *Epool;
+  if constexpr (F32)
+    Epool = dp.Ef;
+  else
+    Epool = dp.E;
+  float ACx = 0.f, ACy = 0.f, ACz = 0.f;
+  if constexpr (F32) {
+    const float *ha = dp.shl + 6 * sA, *hc = dp.shl + 6 * sC;
+    ACx = (ha[0] - hc[0]) + (ha[3] - hc[3]);
+    ACy = (ha[1] - hc[1]) + (ha[4] - hc[4]);
+    ACz = (ha[2] - hc[2]) + (ha[5] - hc[5]);
+  }
 
-  for (int i = gl; i < nab * ncd; i += G) eri[i] = 0.0;
+  for (int i = gl; i < nab * ncd; i += G) eri[i] = Real(0);
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
-    const PZ P4 = dp.pz[ip];
-    const float4 Pf = dp.pf[ip];
-    const double UP = dp.U[ip];
-    const double *EP = dp.E + dp.eoff[ip];
-    for (int i = gl; i < nhab * ncd; i += G) Yh[i] = 0.0;
+    const Real *EP = Epool + dp.eoff[ip];
+    for (int i = gl; i < nhab * ncd; i += G) Yh[i] = Real(0);
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
-      const double *EQ = dp.E + dp.eoff[jq];
-      const PrimQuartet q = prim_quartet(P4, Pf, UP, dp.pz[jq], dp.pf[jq], dp.U[jq]);
-      FK_CHECK(q.T >= 0.0 && q.T == q.T && q.gi <= BOYS_NGRID - 1, 9, jq);
-      boys_seeds_rt<G>(a.boys, q, L, F, R0, gl);
+      const Real *EQ = Epool + dp.eoff[jq];
+      Real X, Y, Z;
+      if constexpr (F32) {
+        const float4 PA = dp.paf[ip], QC = dp.paf[jq];
+        X = PA.x - QC.x + ACx;
+        Y = PA.y - QC.y + ACy;
+        Z = PA.z - QC.z + ACz;
+        const float rs = rsqrtf(PA.w + QC.w);
+        const float alpha = (PA.w * QC.w) * (rs * rs);
+        const float T = alpha * fmaf(X, X, fmaf(Y, Y, Z * Z));
+        boys_seeds_rt_f32<G>(a.boysf, T, dp.Uf[ip] * dp.Uf[jq] * rs, -2.0f * alpha, L, F, R0, gl);
+      } else {
+        const PrimQuartet q = prim_quartet(dp.pz[ip], dp.pf[ip], dp.U[ip], dp.pz[jq], dp.pf[jq], dp.U[jq]);
+        FK_CHECK(q.T >= 0.0 && q.T == q.T && q.gi <= BOYS_NGRID - 1, 9, jq);
+        X = q.X;
+        Y = q.Y;
+        Z = q.Z;
+        boys_seeds_rt<G>(a.boys, q, L, F, R0, gl);
+      }
       group_sync(gmask, G);
-      const double *R = hermite_r<G>(ct, L, q.X, q.Y, q.Z, F, R0, R1, gl, gmask);
+      const Real *R = hermite_r<G, Real>(ct, L, X, Y, Z, F, R0, R1, gl, gmask);
       // ket transform, accumulated over ket primitives
       for (int it = gl; it < nhab * ncd; it += G) {
         const int ph = it / ncd, kc = it - ph * ncd;
@@ -157,13 +215,13 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
         const int ic = kc / nd, id = kc - ic * nd;
         const uint8_t *cc = ct.comp[lc][ic], *dd = ct.comp[ld][id];
         const int Tx = cc[0] + dd[0], Ty = cc[1] + dd[1], Tz = cc[2] + dd[2];
-        const double *Eq = EQ + ct.eoff[ck][kc];
-        double acc = Yh[it];
+        const Real *Eq = EQ + ct.eoff[ck][kc];
+        Real acc = Yh[it];
         int e = 0;
         for (int t = 0; t <= Tx; ++t)
           for (int u = 0; u <= Ty; ++u)
             for (int v = 0; v <= Tz; ++v, ++e) {
-              const double r = R[hidx(tp + t, up + u, vp + v)];
+              const Real r = R[hidx(tp + t, up + u, vp + v)];
               acc = ((t + u + v) & 1) ? fma(-Eq[e], r, acc) : fma(Eq[e], r, acc);
             }
         Yh[it] = acc;
@@ -176,8 +234,8 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
       const int ia = ka / nb, ib = ka - ia * nb;
       const uint8_t *ac = ct.comp[la][ia], *bc = ct.comp[lb][ib];
       const int Tx = ac[0] + bc[0], Ty = ac[1] + bc[1], Tz = ac[2] + bc[2];
-      const double *Ep = EP + ct.eoff[cb][ka];
-      double acc = eri[it];
+      const Real *Ep = EP + ct.eoff[cb][ka];
+      Real acc = eri[it];
       int e = 0;
       for (int t = 0; t <= Tx; ++t)
         for (int u = 0; u <= Ty; ++u)
@@ -189,22 +247,26 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
 
   // digestion into J and K (Sec. 2.3 eight-fold symmetry; J = Jt + Jt^T and
   // K = Kt + Kt^T are formed afterwards by the symmetrisation kernel)
-  double fac = 1.0;
-  if (sA == sB) fac *= 0.5;
-  if (sC == sD) fac *= 0.5;
-  if (P == Q) fac *= 0.5;
+  Real fac = Real(1);
+  if (sA == sB) fac *= Real(0.5);
+  if (sC == sD) fac *= Real(0.5);
+  if (P == Q) fac *= Real(0.5);
   const int N = mv.N;
   const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
-  const double *Dm = mv.D;
-  const double fac2 = 2.0 * fac;
+  const Real *Dm;
+  if constexpr (F32)
+    Dm = mv.Df;
+  else
+    Dm = mv.D;
+  const Real fac2 = Real(2) * fac;
   const int n1 = nab, n2 = n1 + ncd, n3 = n2 + na * nc, n4 = n3 + na * nd, n5 = n4 + nb * nc,
             n6 = n5 + nb * nd;
   for (int o = gl; o < n6; o += G) {
-    double s = 0.0;
+    Real s = Real(0);
     double *dst;
     if (o < n1) {
       const int ia = o / nb, ib = o - ia * nb;
-      const double *e = eri + (size_t)o * ncd;
+      const Real *e = eri + (size_t)o * ncd;
       for (int ic = 0; ic < nc; ++ic)
         for (int id = 0; id < nd; ++id) s = fma(e[ic * nd + id], Dm[(size_t)(fc + ic) * N + fd + id], s);
       dst = mv.J + (size_t)(fa + ia) * N + fb + ib;
@@ -244,9 +306,26 @@ __device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int 
       dst = mv.K + (size_t)(fb + ib) * N + fd + id;
       s *= fac;
     }
-    atomicAdd(dst, s);
+    if constexpr (F32)
+      atomicAdd(dst, f2d_any(s));
+    else
+      atomicAdd(dst, s);
   }
   group_sync(gmask, G);
+}
+
+template <int G>
+__device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int P, int Q, int gl,
+                        unsigned gmask) {
+  const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
+  // density-weighted Schwarz screening over the six shell blocks (Sec. 3.2)
+  const MolView mv = mol_view(a, ab.x);
+  const float b = quartet_bound(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
+  if (b < 0.0f) return;
+  if (b < a.fp32_cutoff_f)
+    quartet_body<G, float>(a, ct, scr, P, Q, gl, gmask, mv);
+  else
+    quartet_body<G, double>(a, ct, scr, P, Q, gl, gmask, mv);
 }
 
 template <int G>
@@ -683,9 +762,9 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
   a.boys = dev_boys();
   a.tabs = dev_class_tables();
   a.mt = nullptr;
-  a.fp32_cutoff = 0.0;  // the group kernels evaluate every quartet in FP64
-  a.fp32_cutoff_f = 0.0f;
-  a.Df = nullptr;
+  a.fp32_cutoff = Df ? fp32_cutoff : 0.0;
+  a.fp32_cutoff_f = (float)a.fp32_cutoff;
+  a.Df = Df;
   a.boysf = dev_boys_f();
   set_screen_args(a, tau, Dshf);
   const dim3 blk(32 * t.warps_per_block);
@@ -720,7 +799,7 @@ cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEnt
   a.tabs = dev_class_tables();
   a.boysf = dev_boys_f();
   a.mt = mt;
-  a.fp32_cutoff = t.reg_cb >= 0 ? fp32_cutoff : 0.0;
+  a.fp32_cutoff = fp32_cutoff;
   a.fp32_cutoff_f = (float)a.fp32_cutoff;
   set_screen_args(a, tau, Dshf);
   const int threads = 32 * t.warps_per_block;

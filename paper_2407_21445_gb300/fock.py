@@ -34,10 +34,14 @@ class fock_basis_desc(ctypes.Structure):
                 ("coefs", ctypes.c_void_p), ("atom", ctypes.c_void_p)]
 
 
+NCLASS = 10  # shell-pair classes ss .. ff
+
+
 class fock_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("fp32_cutoff", ctypes.c_double), ("prune_eps", ctypes.c_double),
                 ("group_override", ctypes.c_int32), ("warp_scratch", ctypes.c_int32), ("reg_max_L", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("tune_isolate", ctypes.c_int32), ("schedule", ctypes.c_int8 * (NCLASS * NCLASS)),
+                ("reserved", ctypes.c_int8 * 4)]
 
 
 _lock = threading.Lock()
@@ -111,6 +115,12 @@ def lib() -> ctypes.CDLL:
             L.fock_hermite_count.restype = i
             L.fock_hermite_e.argtypes = [i, i, d, p, d, p, p]
             L.fock_hermite_e.restype = i
+            L.fock_opts_size.argtypes = []
+            L.fock_opts_size.restype = i
+            L.fock_autotune.argtypes = [p, i, p, ctypes.POINTER(fock_opts), d, i, p, ctypes.POINTER(fock_opts), p]
+            L.fock_autotune.restype = i
+            if L.fock_opts_size() != ctypes.sizeof(fock_opts):
+                raise RuntimeError("fock_opts layout differs between include/fock.h and the binding")
             _lib = L
     return _lib
 
@@ -164,7 +174,7 @@ class _BasisArrays:
 
 
 def make_opts(precision=FOCK_FP64, fp32_cutoff=1e-5, prune_eps=1e-3, group_override=0, warp_scratch=0,
-              reg_max_L=0) -> fock_opts:
+              reg_max_L=0, schedule=None) -> fock_opts:
     o = fock_opts()
     o.reg_max_L = reg_max_L
     o.warp_scratch = warp_scratch
@@ -172,7 +182,16 @@ def make_opts(precision=FOCK_FP64, fp32_cutoff=1e-5, prune_eps=1e-3, group_overr
     o.fp32_cutoff = fp32_cutoff
     o.prune_eps = prune_eps
     o.group_override = group_override
+    if schedule is not None:
+        for k, v in dict(schedule).items():
+            c1, c2 = sorted(k) if isinstance(k, tuple) else divmod(int(k), NCLASS)
+            o.schedule[c1 * NCLASS + c2] = int(v)
     return o
+
+
+def schedule_of(o: fock_opts) -> dict:
+    """Non-default schedule entries {(c1, c2): value} of an options struct."""
+    return {(i // NCLASS, i % NCLASS): int(v) for i, v in enumerate(o.schedule) if v != 0}
 
 
 def fock_shellpairs_build(basis: dict, schwarz_thresh: float, opts: fock_opts | None = None, stream=None):
@@ -211,6 +230,21 @@ def fock_build_jk_batched(handles, Ds, schwarz_thresh: float, Js, Ks, stream=Non
     Kp = (ctypes.c_void_p * n)(*[_tensor_ptr(x, "K").value for x in Ks])
     rc = lib().fock_build_jk_batched(H, n, Dp, float(schwarz_thresh), Jp, Kp, _stream_handle(stream))
     _check(rc, "fock_build_jk_batched")
+
+
+def fock_autotune(bases, Ds, schwarz_thresh: float, opts: fock_opts | None = None, reps: int = 3, stream=None):
+    """Measured per-class-pair schedule for the workload (bases, device
+    densities Ds); returns (tuned fock_opts, [ms with base, ms tuned])."""
+    n = len(bases)
+    arrs = [_BasisArrays(b) for b in bases]
+    descs = (ctypes.c_void_p * n)(*[ctypes.cast(ctypes.pointer(a.desc), ctypes.c_void_p).value for a in arrs])
+    Dp = (ctypes.c_void_p * n)(*[_tensor_ptr(x, "D").value for x in Ds])
+    out = fock_opts()
+    ms = np.zeros(2)
+    rc = lib().fock_autotune(descs, n, Dp, ctypes.byref(opts) if opts is not None else None, float(schwarz_thresh),
+                             int(reps), _stream_handle(stream), ctypes.byref(out), _np_ptr(ms))
+    _check(rc, "fock_autotune")
+    return out, [float(ms[0]), float(ms[1])]
 
 
 def fock_work_stats(handle, D_host: np.ndarray, schwarz_thresh: float) -> dict:

@@ -23,9 +23,9 @@ def env():
     return torch, fk
 
 
-def mixed_jk(env, basis, D, tau, cutoff=1e-5):
+def mixed_jk(env, basis, D, tau, cutoff=1e-5, **kw):
     torch, fk = env
-    b = fk.JKBuilder(basis, tau, fk.make_opts(precision=fk.FOCK_MIXED, fp32_cutoff=cutoff))
+    b = fk.JKBuilder(basis, tau, fk.make_opts(precision=fk.FOCK_MIXED, fp32_cutoff=cutoff, **kw))
     Dt = torch.tensor(D, device="cuda", dtype=torch.float64)
     J, K = b.build(Dt)
     torch.cuda.synchronize()
@@ -91,3 +91,18 @@ def test_mixed_water64_blocks(env):
     for (a, b), jb, kb in zip(pairs, Jb, Kb):
         assert np.abs(J[offs[a]:offs[a + 1], offs[b]:offs[b + 1]] - jb).max() <= TOL_MIXED
         assert np.abs(K[offs[a]:offs[a + 1], offs[b]:offs[b + 1]] - kb).max() <= TOL_MIXED
+
+
+@pytest.mark.parametrize("group", [0, 1, 4, 32])
+def test_mixed_group_kernels(env, group):
+    """Every class pair on the group-cooperative kernels (no register
+    kernels), FP32 quartets included, for several group sizes."""
+    rng = np.random.Generator(np.random.PCG64(301 + group))
+    bas = molgen.random_shells(rng, [0, 1, 2, 3, 0, 1, 2, 0], spread=3.0, kmax=3)
+    n = oracle.nbf(bas)
+    D = rng.uniform(-1, 1, (n, n))
+    D = 0.5 * (D + D.T)
+    J, K, st = mixed_jk(env, bas, D, 1e-11, cutoff=1e-4, reg_max_L=-1, group_override=group)
+    Jo, Ko = oracle.jk(bas, D, 1e-11)
+    check(J, K, Jo, Ko, D)
+    assert st["quartets_fp32"] > 0

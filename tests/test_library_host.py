@@ -152,3 +152,57 @@ def test_build_validation_codes():
     assert L.fock_nbasis(None) == -1
     assert L.fock_boys_host(13, 1.0, None) == 1
     assert L.fock_hermite_count(4, 0) == -1
+
+
+def test_opts_layout_and_schedule_validation():
+    """The binding's fock_opts matches the library's; schedule entries and
+    tune_isolate outside their documented values are rejected before any
+    device work."""
+    L = fb.lib()
+    assert L.fock_opts_size() == ctypes.sizeof(fb.fock_opts)
+    assert fb.fock_opts.schedule.offset == 40 and ctypes.sizeof(fb.fock_opts) == 144
+    good = molgen.problem(0).basis
+    arr = _desc(good)
+
+    def build(o):
+        out = ctypes.c_void_p()
+        return L.fock_shellpairs_build(ctypes.byref(arr.desc), ctypes.byref(o), 1e-10, None, ctypes.byref(out))
+
+    for v in (3, -2, 64, 5):
+        o = fk.make_opts(schedule={(0, 5): v})
+        assert build(o) == 1, v
+    o = fk.make_opts()
+    o.tune_isolate = 2
+    assert build(o) == 1
+    o = fk.make_opts(schedule={(5, 2): 8, 12: -1})
+    assert fk.schedule_of(o) == {(2, 5): 8, (1, 2): -1}
+    assert L.fock_autotune(None, 1, None, None, 1e-10, 3, None, None, None) == 1
+    D = (ctypes.c_void_p * 1)(1)
+    descs = (ctypes.c_void_p * 1)(ctypes.cast(ctypes.pointer(arr.desc), ctypes.c_void_p).value)
+    res = fb.fock_opts()
+    for reps in (0, 101):
+        assert L.fock_autotune(descs, 1, D, None, 1e-10, reps, None, ctypes.byref(res), None) == 1
+    assert L.fock_autotune(descs, 0, D, None, 1e-10, 3, None, ctypes.byref(res), None) == 1
+
+
+def test_autotune_cache_roundtrip(tmp_path):
+    """A stored schedule is found again by workload shape (other geometry,
+    same composition) and not for another composition or device."""
+    from paper_2407_21445_gb300 import autotune
+    p0 = molgen.problem(0)
+    bases = [p0.basis]
+    cache = str(tmp_path / "tune.json")
+    key = autotune.workload_key(bases, 1e-12, None, "GPU-A")
+    with open(cache, "w") as f:
+        json.dump({key: {"ms_base": 2.0, "ms_tuned": 1.5, "schedule": {"0,5": 8, "2,2": -1}}}, f)
+    moved = dict(p0.basis)
+    moved["center"] = p0.basis["center"] + 1.0
+    o, rec = autotune.tuned_opts([moved], None, 1e-12, cache=cache, device_name="GPU-A")
+    assert rec["cached"] and fk.schedule_of(o) == {(0, 5): 8, (2, 2): -1} and o.tune_isolate == 0
+    assert autotune.workload_key(bases, 1e-12, None, "GPU-B") != key
+    assert autotune.workload_key(bases, 1e-10, None, "GPU-A") != key
+    other = molgen.problem(0).basis
+    other = dict(other)
+    other["nprim"] = other["nprim"].copy()
+    other["nprim"][0] = 2
+    assert autotune.workload_key([other], 1e-12, None, "GPU-A") != key
