@@ -43,12 +43,17 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--carbons", type=int, default=20, help="alkane length for --config 1 (profiling cases)")
+    ap.add_argument("--waters", type=int, default=64, help="water molecules for --config 2 (334: 1,002 atoms)")
     ap.add_argument("--nmol", type=int, default=256, help="molecules of the batched workload (--config 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warp-scratch", type=int, default=0, help="shared-memory doubles per warp (0 = library default)")
     ap.add_argument("--reg-max-l", type=int, default=0, help="largest total L served by register kernels (0 = default)")
     ap.add_argument("--fp32-cutoff", type=float, default=1e-5, help="mixed leg: FP32 below this quartet bound")
     ap.add_argument("--no-mixed-leg", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="built-in schedule rule instead of the measured one")
+    ap.add_argument("--tune-cache", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                         "paper_2407_21445_gb300", "_build", "tune_cache.json"))
+    ap.add_argument("--tune-nmol", type=int, default=2, help="--config 3: molecules the schedule is measured on")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the headline leg (mixed: FP32 below --fp32-cutoff)")
     return ap.parse_args()
@@ -162,7 +167,7 @@ def run_reference(args, rank, world):
     import oracle
     if rank != 0:
         return
-    p = molgen.problem(args.config, carbons=args.carbons)
+    p = molgen.problem(args.config, carbons=args.carbons, waters=args.waters)
     cnt = oracle.count(p.basis, p.D, p.tau)
     t0 = time.perf_counter()
     oracle.jk_sample(p.basis, p.D, p.tau, 64)
@@ -189,6 +194,21 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def tuned(args, fk, bases, Ds, tau, prec):
+    """Options for the timed builds: the measured per-class-pair schedule
+    (fock_autotune, cached per workload shape and GPU) unless --no-autotune;
+    tuning runs before, and outside, every timed region."""
+    base = fk.make_opts(precision=prec, fp32_cutoff=args.fp32_cutoff, warp_scratch=args.warp_scratch,
+                        reg_max_L=args.reg_max_l)
+    if args.no_autotune:
+        return base, {"source": "built-in rule"}
+    from paper_2407_21445_gb300 import autotune
+    o, rec = autotune.tuned_opts(bases, Ds, tau, base, cache=args.tune_cache, reps=3)
+    return o, {"source": "autotuned" + (" (cached)" if rec["cached"] else ""), "tuned_on_molecules": len(bases),
+               "ms_built_in_rule": rec["ms_base"], "ms_tuned": rec["ms_tuned"],
+               "class_pairs_changed": len(rec["schedule"])}
+
+
 def run_batched(args, fk, torch, dev, stream, world, rank, dist):
     """256 molecules of uneven size (TZ-shaped basis up to f) per step through
     fock_build_jk_batched; FP64 headline plus a mixed-precision leg."""
@@ -197,10 +217,12 @@ def run_batched(args, fk, torch, dev, stream, world, rank, dist):
     tau = probs[0].tau
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    tunes = {}
+
     def setup(prec):
-        bs = [fk.JKBuilder(p.basis, tau, fk.make_opts(precision=prec, fp32_cutoff=args.fp32_cutoff,
-                                                     warp_scratch=args.warp_scratch, reg_max_L=args.reg_max_l))
-              for p in probs]
+        k = max(1, min(args.tune_nmol, len(probs)))
+        opts, tunes[prec] = tuned(args, fk, [p.basis for p in probs[:k]], Ds[:k], tau, prec)
+        bs = [fk.JKBuilder(p.basis, tau, opts) for p in probs]
         return bs
 
     def timed(bs, Ds, Js, Ks):
@@ -265,7 +287,8 @@ def run_batched(args, fk, torch, dev, stream, world, rank, dist):
         mixed = {"ms_per_step": mms, "value": eris / (mms * 1e-3), "unit": UNIT, "speedup_vs_fp64": ms / mms,
                  "fp32_cutoff": args.fp32_cutoff, "max_abs_diff_vs_fp64": err,
                  "fp32_quartet_share": q32 / max(q, 1.0), "fp32_flop_share": f32 / max(flops, 1.0),
-                 "fp64_flop_frac_of_peak": (flops - f32) / (mms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+                 "fp64_flop_frac_of_peak": (flops - f32) / (mms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                 "schedule": tunes.get(fk.FOCK_MIXED)}
     if rank == 0:
         achieved = flops / (ms * 1e-3) / 1e12
         nbf = [p.nbf for p in probs]
@@ -278,7 +301,7 @@ def run_batched(args, fk, torch, dev, stream, world, rank, dist):
                            "molecules": len(probs), "nbf_total": int(sum(nbf)), "nbf_min": int(min(nbf)),
                            "nbf_max": int(max(nbf)), "schwarz_thresh": tau, "eris_per_step": int(eris),
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",
-                           "precision": "fp64"},
+                           "precision": "fp64", "schedule": tunes.get(fk.FOCK_FP64)},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None},
                 "e2e": {"value": world * eris / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
@@ -310,13 +333,13 @@ def main():
 
     if args.config == 3:
         return run_batched(args, fk, torch, dev, stream, world, rank, dist)
-    p = molgen.problem(args.config, carbons=args.carbons)
+    p = molgen.problem(args.config, carbons=args.carbons, waters=args.waters)
     prec = fk.FOCK_MIXED if args.precision == "mixed" else fk.FOCK_FP64
-    builder = fk.JKBuilder(p.basis, p.tau, fk.make_opts(precision=prec, fp32_cutoff=args.fp32_cutoff,
-                                                        warp_scratch=args.warp_scratch, reg_max_L=args.reg_max_l))
+    D = torch.tensor(p.D, device=dev, dtype=torch.float64)
+    opts, tune = tuned(args, fk, [p.basis], [D], p.tau, prec)
+    builder = fk.JKBuilder(p.basis, p.tau, opts)
     st = builder.stats(p.D)
     nk = fk.fock_kernels_per_build(builder.handle)
-    D = torch.tensor(p.D, device=dev, dtype=torch.float64)
     J = torch.empty_like(D)
     K = torch.empty_like(D)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -378,8 +401,8 @@ def main():
     # ---- mixed-precision leg on the same workload (extra key) --------------
     mixed = None
     if not args.no_mixed_leg and args.precision == "fp64":
-        mb = fk.JKBuilder(p.basis, p.tau, fk.make_opts(precision=fk.FOCK_MIXED, fp32_cutoff=args.fp32_cutoff,
-                                                      warp_scratch=args.warp_scratch, reg_max_L=args.reg_max_l))
+        mopts, mtune = tuned(args, fk, [p.basis], [D], p.tau, fk.FOCK_MIXED)
+        mb = fk.JKBuilder(p.basis, p.tau, mopts)
         mst = mb.stats(p.D)
         builder.build(D, J, K)
         Jm = torch.empty_like(D)
@@ -401,7 +424,7 @@ def main():
                  "speedup_vs_fp64": ms / mms, "fp32_cutoff": args.fp32_cutoff,
                  "max_abs_diff_vs_fp64": err, "trace_diff_vs_fp64": trd,
                  "fp32_quartet_share": mst["quartets_fp32"] / max(1.0, mst["quartets_evaluated"]),
-                 "fp32_flop_share": mst["flops_model_fp32"] / max(1.0, mst["flops_model"])}
+                 "fp32_flop_share": mst["flops_model_fp32"] / max(1.0, mst["flops_model"]), "schedule": mtune}
         mb.close()
 
     if rank == 0:
@@ -411,7 +434,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "s_per_iteration": ms * 1e-3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f64+f32",
-            "data": "synthetic", "config": workload_config(p, st, args.precision),
+            "data": "synthetic", "config": dict(workload_config(p, st, args.precision), schedule=tune),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": profile_traffic(kernel_hash()),
                          "peak_note": "FP64 pipe, derived 152 SMs x 2 FMA/clk x 2.07 GHz; achieved = modelled "

@@ -239,6 +239,9 @@ FOCK_API int32_t fock_kernels_per_build(const fock_shellpairs *sp);
  *   *tuned: receives base with the chosen schedule (tune_isolate = 0).
  *   ms[0], ms[1] (may be NULL): median build time in milliseconds with the
  *   base and with the tuned schedule; *tuned is the faster of the two.
+ *   pair_ms (may be NULL, FOCK_NCLASS * FOCK_NCLASS doubles): the time of
+ *   each class pair with the base schedule, launched apart (the smallest
+ *   over the reps), at the index of the schedule entry; 0 where absent.
  * Allocates and frees its own J, K and handles; synchronises `stream`;
  * takes seconds (7 candidate plans, (reps + 1) builds each).
  * Errors: as fock_shellpairs_build and fock_build_jk; FOCK_ERR_INVALID_ARG
@@ -246,7 +249,7 @@ FOCK_API int32_t fock_kernels_per_build(const fock_shellpairs *sp);
  */
 FOCK_API fock_status fock_autotune(const fock_basis_desc *const *descs, int32_t nmol, const double *const *D,
                                    const fock_opts *base, double schwarz_thresh, int32_t reps,
-                                   cudaStream_t stream, fock_opts *tuned, double *ms);
+                                   cudaStream_t stream, fock_opts *tuned, double *ms, double *pair_ms);
 
 /*
  * FP64 one-electron integrals for the RHF driver (Sec. 2.2: F = h + J - K/2,

@@ -313,16 +313,17 @@ CONFIG_NAMES = {
 }
 
 
-def problem(config: int, seed: int = 0, carbons: int = 20) -> Problem:
+def problem(config: int, seed: int = 0, carbons: int = 20, waters: int = 64) -> Problem:
     """The seeded synthetic workload for config 0 (water trimer), 1 (C20H42,
-    or another zigzag alkane length via `carbons`) or 2 ((H2O)64 sphere)."""
+    or another zigzag alkane length via `carbons`) or 2 ((H2O)64 sphere, or
+    another cluster size via `waters`: 334 gives the 1,002-atom cluster)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     if config == 0:
         mol, tau = water_chain_cluster(3, rng), 1e-12
     elif config == 1:
         mol, tau = alkane_zigzag(carbons), 1e-10
     elif config == 2:
-        mol, tau = water_sphere_cluster(64, rng), 1e-10
+        mol, tau = water_sphere_cluster(waters, rng), 1e-10
     else:
         raise ValueError(f"unknown config {config}")
     basis = make_basis(mol, basis_set("dz", seed))
@@ -330,7 +331,9 @@ def problem(config: int, seed: int = 0, carbons: int = 20) -> Problem:
     name = CONFIG_NAMES[config]
     if config == 1 and carbons != 20:
         name = name.replace("C20H42", f"C{carbons}H{2 * carbons + 2}")
-    return Problem(name, mol, basis, D, tau, dict(config=config, seed=seed, carbons=carbons))
+    if config == 2 and waters != 64:
+        name = name.replace("(H2O)64", f"(H2O){waters}")
+    return Problem(name, mol, basis, D, tau, dict(config=config, seed=seed, carbons=carbons, waters=waters))
 
 
 def batch_molecules(n: int = 256, seed: int = 0, min_atoms: int = 5, max_atoms: int = 40) -> list:

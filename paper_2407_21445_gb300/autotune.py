@@ -60,9 +60,10 @@ def tuned_opts(bases, Ds, schwarz_thresh: float, opts: fock.fock_opts | None = N
             c1, c2 = (int(x) for x in k.split(","))
             out.schedule[c1 * fock.NCLASS + c2] = int(v)
         return out, dict(rec, cached=True)
-    out, ms = fock.fock_autotune(bases, Ds, schwarz_thresh, base, reps, stream)
+    out, ms, pair = fock.fock_autotune(bases, Ds, schwarz_thresh, base, reps, stream)
     rec = {"ms_base": ms[0], "ms_tuned": ms[1],
-           "schedule": {f"{a},{b}": v for (a, b), v in fock.schedule_of(out).items()}}
+           "schedule": {f"{a},{b}": v for (a, b), v in fock.schedule_of(out).items()},
+           "pair_ms_base": {f"{a},{b}": v for (a, b), v in pair.items()}}
     if cache:
         db = _load(cache)
         db[key] = rec

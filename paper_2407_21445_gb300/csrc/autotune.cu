@@ -122,7 +122,7 @@ fock_status build_time(Workload &w, const Handles &hs, int reps, double *ms) {
   return FOCK_OK;
 }
 
-fock_status tune(Workload &w, const fock_opts &base, int reps, fock_opts *tuned, double *ms) {
+fock_status tune(Workload &w, const fock_opts &base, int reps, fock_opts *tuned, double *ms, double *pair_ms) {
   // the base schedule, class pairs apart
   fock_opts iso = base;
   iso.tune_isolate = 1;
@@ -133,6 +133,8 @@ fock_status tune(Workload &w, const fock_opts &base, int reps, fock_opts *tuned,
     if (s == FOCK_OK) s = tag_times(w, hs, reps, t_base);
     if (s != FOCK_OK) return s;
   }
+  if (pair_ms)
+    for (int i = 0; i < kNPairs; ++i) pair_ms[i] = t_base[i + 1];
   std::vector<double> best_t(t_base);
   std::vector<int> best_c(kNPairs, 0);
   for (int c : kCand) {
@@ -186,7 +188,7 @@ fock_status tune(Workload &w, const fock_opts &base, int reps, fock_opts *tuned,
 
 extern "C" fock_status fock_autotune(const fock_basis_desc *const *descs, int32_t nmol, const double *const *D,
                                      const fock_opts *base, double schwarz_thresh, int32_t reps,
-                                     cudaStream_t stream, fock_opts *tuned, double *ms) {
+                                     cudaStream_t stream, fock_opts *tuned, double *ms, double *pair_ms) {
   if (!descs || !D || !tuned || nmol < 1 || reps < 1 || reps > 100) return FOCK_ERR_INVALID_ARG;
   for (int i = 0; i < nmol; ++i)
     if (!descs[i] || !D[i]) return FOCK_ERR_INVALID_ARG;
@@ -213,7 +215,7 @@ extern "C" fock_status fock_autotune(const fock_basis_desc *const *descs, int32_
     w.J.push_back(buf + off[i]);
     w.K.push_back(buf + off[i] + n2);
   }
-  fock_status s = tune(w, b, reps, tuned, ms);
+  fock_status s = tune(w, b, reps, tuned, ms, pair_ms);
   cudaStreamSynchronize(stream);
   cudaFree(buf);
   return s;

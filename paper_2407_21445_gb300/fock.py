@@ -117,7 +117,8 @@ def lib() -> ctypes.CDLL:
             L.fock_hermite_e.restype = i
             L.fock_opts_size.argtypes = []
             L.fock_opts_size.restype = i
-            L.fock_autotune.argtypes = [p, i, p, ctypes.POINTER(fock_opts), d, i, p, ctypes.POINTER(fock_opts), p]
+            L.fock_autotune.argtypes = [p, i, p, ctypes.POINTER(fock_opts), d, i, p, ctypes.POINTER(fock_opts), p,
+                                        p]
             L.fock_autotune.restype = i
             if L.fock_opts_size() != ctypes.sizeof(fock_opts):
                 raise RuntimeError("fock_opts layout differs between include/fock.h and the binding")
@@ -234,17 +235,19 @@ def fock_build_jk_batched(handles, Ds, schwarz_thresh: float, Js, Ks, stream=Non
 
 def fock_autotune(bases, Ds, schwarz_thresh: float, opts: fock_opts | None = None, reps: int = 3, stream=None):
     """Measured per-class-pair schedule for the workload (bases, device
-    densities Ds); returns (tuned fock_opts, [ms with base, ms tuned])."""
+    densities Ds); returns (tuned fock_opts, [ms with base, ms tuned],
+    {(c1, c2): ms of that class pair with the base schedule})."""
     n = len(bases)
     arrs = [_BasisArrays(b) for b in bases]
     descs = (ctypes.c_void_p * n)(*[ctypes.cast(ctypes.pointer(a.desc), ctypes.c_void_p).value for a in arrs])
     Dp = (ctypes.c_void_p * n)(*[_tensor_ptr(x, "D").value for x in Ds])
     out = fock_opts()
     ms = np.zeros(2)
+    pair = np.zeros(NCLASS * NCLASS)
     rc = lib().fock_autotune(descs, n, Dp, ctypes.byref(opts) if opts is not None else None, float(schwarz_thresh),
-                             int(reps), _stream_handle(stream), ctypes.byref(out), _np_ptr(ms))
+                             int(reps), _stream_handle(stream), ctypes.byref(out), _np_ptr(ms), _np_ptr(pair))
     _check(rc, "fock_autotune")
-    return out, [float(ms[0]), float(ms[1])]
+    return out, [float(ms[0]), float(ms[1])], {(i // NCLASS, i % NCLASS): float(v) for i, v in enumerate(pair) if v > 0}
 
 
 def fock_work_stats(handle, D_host: np.ndarray, schwarz_thresh: float) -> dict:

@@ -63,8 +63,9 @@ def test_autotune_single(env):
     torch, fk = env
     p = molgen.problem(0)
     Dt = torch.tensor(p.D, device="cuda", dtype=torch.float64)
-    o, ms = fk.fock_autotune([p.basis], [Dt], p.tau, None, reps=2)
+    o, ms, pair = fk.fock_autotune([p.basis], [Dt], p.tau, None, reps=2)
     assert ms[0] > 0 and ms[1] > 0 and o.tune_isolate == 0
+    assert pair and all(a <= b for a, b in pair) and sum(pair.values()) < 3 * ms[0]
     assert set(fk.schedule_of(o).values()) <= {-1, 1, 2, 4, 8, 16, 32}
     J, K, _ = _jk(env, p.basis, p.D, p.tau, o)
     Jo, Ko = oracle.jk(p.basis, p.D, p.tau)

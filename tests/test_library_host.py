@@ -176,13 +176,13 @@ def test_opts_layout_and_schedule_validation():
     assert build(o) == 1
     o = fk.make_opts(schedule={(5, 2): 8, 12: -1})
     assert fk.schedule_of(o) == {(2, 5): 8, (1, 2): -1}
-    assert L.fock_autotune(None, 1, None, None, 1e-10, 3, None, None, None) == 1
+    assert L.fock_autotune(None, 1, None, None, 1e-10, 3, None, None, None, None) == 1
     D = (ctypes.c_void_p * 1)(1)
     descs = (ctypes.c_void_p * 1)(ctypes.cast(ctypes.pointer(arr.desc), ctypes.c_void_p).value)
     res = fb.fock_opts()
     for reps in (0, 101):
-        assert L.fock_autotune(descs, 1, D, None, 1e-10, reps, None, ctypes.byref(res), None) == 1
-    assert L.fock_autotune(descs, 0, D, None, 1e-10, 3, None, ctypes.byref(res), None) == 1
+        assert L.fock_autotune(descs, 1, D, None, 1e-10, reps, None, ctypes.byref(res), None, None) == 1
+    assert L.fock_autotune(descs, 0, D, None, 1e-10, 3, None, ctypes.byref(res), None, None) == 1
 
 
 def test_autotune_cache_roundtrip(tmp_path):
