@@ -94,14 +94,72 @@ def run(n: int, ntrain: int, out: str, epochs: int, seed: int = 0, tau: float = 
     return report
 
 
+def sensitivity(params: str, out: str, n: int = 500, ntrain: int = 400, nmol: int = 10, seed: int = 0,
+                tau: float = 1e-10, scales=(1.0, 0.3, 0.1, 0.03, 0.01, 1e-3, 1e-4), log=print):
+    """How accurate must a guess be?  On the first nmol held-out conformations
+    (same seeded split as run()): SCF from the idempotent projection of
+    D_conv + s (D_SAD - D_conv) for each scale s, the Frobenius errors
+    |D0 - D_conv| of the SAD and the trained-MLP guesses, and the MLP's
+    iterations.  Writes out/sensitivity.json."""
+    os.makedirs(out, exist_ok=True)
+    table = molgen.basis_set("dz", seed)
+    mols = molgen.scf_conformations(n, seed)
+    rng = np.random.Generator(np.random.PCG64(50_000 + seed))
+    order = rng.permutation(n)
+    test_idx = sorted(order[ntrain:].tolist())[:nmol]
+    z = np.load(params)
+    lg = G.LearnedGuess(hidden=128, max_batch=8192, seed=seed)
+    lg.net.set_params(z["params"])
+    lg.mu, lg.sd = z["mu"], z["sd"]
+    rows = []
+    for i in test_idx:
+        mol = mols[i]
+        basis = molgen.make_basis(mol, table)
+        rhf = RHF(mol.Z.astype(float), mol.coords, basis, tau=tau)
+        Ds = sad_guess(mol, table)
+        r = rhf.run(Ds)
+        Dc = r.D
+        Dm = lg.guess(mol, basis, rhf, Ds.cpu().numpy())
+        rm = rhf.run(Dm)
+        Dsp = G.project_idempotent(Ds, rhf.S, rhf.X, rhf.nocc)
+        row = dict(index=i, nbf=int(rhf.S.shape[0]), sad_it=r.iterations, mlp_it=rm.iterations,
+                   err_sad=float(torch.linalg.norm(Ds - Dc)), err_sad_projected=float(torch.linalg.norm(Dsp - Dc)),
+                   err_mlp=float(torch.linalg.norm(Dm - Dc)), scaled={})
+        for sc in scales:
+            D0 = G.project_idempotent(Dc + sc * (Ds - Dc), rhf.S, rhf.X, rhf.nocc)
+            rs = rhf.run(D0)
+            row["scaled"][str(sc)] = dict(it=rs.iterations, err=float(torch.linalg.norm(D0 - Dc)),
+                                          dE=abs(rs.energy - r.energy))
+        rows.append(row)
+        log(f"{i}: sad {row['sad_it']} mlp {row['mlp_it']} err sad {row['err_sad']:.3g} mlp {row['err_mlp']:.3g} "
+            + " ".join(f"{k}:{v['it']}" for k, v in row["scaled"].items()))
+    summ = {"mean_sad_it": float(np.mean([r["sad_it"] for r in rows])),
+            "mean_mlp_it": float(np.mean([r["mlp_it"] for r in rows])),
+            "mean_err_sad": float(np.mean([r["err_sad"] for r in rows])),
+            "mean_err_mlp": float(np.mean([r["err_mlp"] for r in rows])),
+            "mean_it_by_scale": {str(sc): float(np.mean([r["scaled"][str(sc)]["it"] for r in rows])) for sc in scales},
+            "mean_err_by_scale": {str(sc): float(np.mean([r["scaled"][str(sc)]["err"] for r in rows]))
+                                  for sc in scales},
+            "rows": rows}
+    with open(os.path.join(out, "sensitivity.json"), "w") as f:
+        json.dump(summ, f, indent=1)
+    return summ
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--sensitivity", default=None, metavar="PARAMS_NPZ",
+                    help="instead of training: guess-accuracy study with a trained network")
     ap.add_argument("--n", type=int, default=500)
     ap.add_argument("--train", type=int, default=400)
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default="guess_run")
     a = ap.parse_args()
+    if a.sensitivity:
+        rep = sensitivity(a.sensitivity, a.out, a.n, a.train, seed=a.seed)
+        print(json.dumps({k: v for k, v in rep.items() if k != "rows"}))
+        return
     rep = run(a.n, a.train, a.out, a.epochs, a.seed)
     print(json.dumps({k: v for k, v in rep.items() if k != "per_molecule"}))
 

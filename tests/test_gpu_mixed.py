@@ -98,7 +98,7 @@ def test_mixed_group_kernels(env, group):
     """Every class pair on the group-cooperative kernels (no register
     kernels), FP32 quartets included, for several group sizes."""
     rng = np.random.Generator(np.random.PCG64(301 + group))
-    bas = molgen.random_shells(rng, [0, 1, 2, 3, 0, 1, 2, 0], spread=3.0, kmax=3)
+    bas = molgen.random_shells(rng, [0, 1, 2, 3, 0, 1, 2, 0], spread=6.0, kmax=3)
     n = oracle.nbf(bas)
     D = rng.uniform(-1, 1, (n, n))
     D = 0.5 * (D + D.T)
