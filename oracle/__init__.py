@@ -24,7 +24,9 @@ _lock = threading.Lock()
 _lib = None
 
 SCREEN_NONE, SCREEN_SCHWARZ, SCREEN_DENSITY = 0, 1, 2
-EPS_PRUNE = 1e-3  # primitive pair dropped iff G_[ab] * Gmax < tau * EPS_PRUNE
+# primitive pair dropped iff G_[ab] * Gmax < tau * EPS_PRUNE; with the density
+# test (SCREEN_DENSITY), primitive quartet skipped iff G_[ab] G_[cd] Dmax < tau * EPS_PRUNE
+EPS_PRUNE = 1e-3
 
 
 def build(force: bool = False) -> str:

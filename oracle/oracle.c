@@ -25,7 +25,11 @@
  *     or G_ab G_cd Dmax < tau with Dmax the largest |D| over the six shell
  *     blocks ab, ac, ad, bc, bd, cd (in-kernel test), both Sec. 3.2;
  *   - a primitive pair is dropped iff G_[ab] * Gmax < tau * eps_p, Gmax the
- *     largest contracted G_ab (primitive-level pruning, Sec. 3.2).
+ *     largest contracted G_ab (primitive-level pruning, Sec. 3.2);
+ *   - inside a contracted quartet that passes, a primitive quartet [ab|cd]
+ *     is skipped iff G_[ab] * G_[cd] * Dmax < tau * eps_p, Dmax the six-block
+ *     maximum above (screening with the primitive Cauchy-Schwarz bound, Sec.
+ *     3.2, at the level of primitive integrals as in the MMD scheme, Sec. 3.3).
  *
  * Every J/K accumulation uses Neumaier-compensated sums.
  *
@@ -337,9 +341,15 @@ typedef struct {
 /* Contracted shell-quartet ERIs (ab|cd), normalised Cartesian functions.
  * out[((ia*nb+ib)*nc+ic)*nd+id].  Primitive pairs absent from the keep masks
  * are skipped.  Optional prim restriction (pi,pj) on the bra and ket pair for
- * primitive Schwarz factors: pass -1 to use all. */
+ * primitive Schwarz factors: pass -1 to use all.
+ * Primitive-quartet screening (Sec. 3.2, primitive Cauchy-Schwarz bound,
+ * applied at the level of primitive integrals as the MMD scheme of Sec. 3.3
+ * does): with gab, gcd the primitive factors G_[ab], G_[cd] of the two pairs
+ * (indexed like the keep masks), the primitive quartet [ab|cd] is skipped
+ * iff G_[ab] * G_[cd] * dm < thr.  gab == NULL: no primitive-quartet test. */
 static void or_shell_quartet(const or_ctx *X, or_work *w, int sa, int sb, int sc, int sd,
-                             int bra_prim, int ket_prim, double *out) {
+                             int bra_prim, int ket_prim, const double *gab, const double *gcd, double dm,
+                             double thr, double *out) {
   const or_basis *B = X->B;
   int la = B->l[sa], lb = B->l[sb], lc = B->l[sc], ld = B->l[sd];
   const double *A = B->center + 3 * sa, *Bc = B->center + 3 * sb, *C = B->center + 3 * sc,
@@ -359,6 +369,7 @@ static void or_shell_quartet(const or_ctx *X, or_work *w, int sa, int sb, int sc
           int pkl = k * Kd + l;
           if (ket_prim >= 0 && pkl != ket_prim) continue;
           if (!((kcd >> pkl) & 1)) continue;
+          if (gab && gab[pij] * gcd[pkl] * dm < thr) continue;
           double s = X->coef[oa + i] * X->coef[ob + j] * X->coef[oc + k] * X->coef[od + l];
           or_vrr_prim(w, la + lb, lc + ld, B->exps[oa + i], A, B->exps[ob + j], Bc,
                       B->exps[oc + k], C, B->exps[od + l], D, s);
@@ -500,7 +511,7 @@ int oracle_shell_eri(int nshell, const double *center, const int32_t *l, const i
   if (or_ctx_init(&X, &B)) return 1;
   or_work w;
   or_work_alloc(&w);
-  or_shell_quartet(&X, &w, sa, sb, sc, sd, -1, -1, out);
+  or_shell_quartet(&X, &w, sa, sb, sc, sd, -1, -1, NULL, NULL, 0.0, 0.0, out);
   or_work_free(&w);
   or_ctx_free(&X);
   return 0;
@@ -524,7 +535,7 @@ static void or_schwarz(const or_ctx *X, double *G, double *Gp) {
     for (int sa = 0; sa < ns; ++sa)
       for (int sb = 0; sb <= sa; ++sb) {
         int na = OR_NC(B->l[sa]), nb = OR_NC(B->l[sb]), nab = na * nb;
-        or_shell_quartet(X, &w, sa, sb, sa, sb, -1, -1, buf);
+        or_shell_quartet(X, &w, sa, sb, sa, sb, -1, -1, NULL, NULL, 0.0, 0.0, buf);
         double mx = 0.0;
         for (int k = 0; k < nab; ++k) mx = fmax(mx, fabs(buf[k * nab + k]));
         G[(size_t)sa * ns + sb] = G[(size_t)sb * ns + sa] = sqrt(mx);
@@ -532,7 +543,7 @@ static void or_schwarz(const or_ctx *X, double *G, double *Gp) {
         for (int i = 0; i < Ka; ++i)
           for (int j = 0; j < Kb; ++j) {
             int p = i * Kb + j;
-            or_shell_quartet(X, &w, sa, sb, sa, sb, p, p, buf);
+            or_shell_quartet(X, &w, sa, sb, sa, sb, p, p, NULL, NULL, 0.0, 0.0, buf);
             double m2 = 0.0;
             for (int k = 0; k < nab; ++k) m2 = fmax(m2, fabs(buf[k * nab + k]));
             double g = sqrt(m2);
@@ -619,6 +630,31 @@ static void or_setup_free(or_jk_setup *S) {
   or_ctx_free(&S->X);
 }
 
+/* max |D| over the six shell blocks of (ab|cd) (Sec. 3.2) */
+static double or_dmax(const or_jk_setup *S, int a, int b, int c, int d) {
+  int ns = S->X.B->nshell;
+  const double *Q = S->Dsh;
+  double dm = Q[(size_t)a * ns + b];
+  dm = fmax(dm, Q[(size_t)c * ns + d]);
+  dm = fmax(dm, Q[(size_t)a * ns + c]);
+  dm = fmax(dm, Q[(size_t)a * ns + d]);
+  dm = fmax(dm, Q[(size_t)b * ns + c]);
+  dm = fmax(dm, Q[(size_t)b * ns + d]);
+  return dm;
+}
+
+/* The contracted quartet (ab|cd) of a J/K loop: density-weighted primitive
+ * quartet screening with the pruning factor eps_p (mode M2 only). */
+static void or_jk_quartet(const or_jk_setup *S, or_work *w, int a, int b, int c, int d, double eps_p,
+                          double *eri) {
+  int ns = S->X.B->nshell;
+  if (S->mode == OR_SCREEN_DENSITY && eps_p > 0.0)
+    or_shell_quartet(&S->X, w, a, b, c, d, -1, -1, S->Gp + ((size_t)a * ns + b) * 64,
+                     S->Gp + ((size_t)c * ns + d) * 64, or_dmax(S, a, b, c, d), S->tau * eps_p, eri);
+  else
+    or_shell_quartet(&S->X, w, a, b, c, d, -1, -1, NULL, NULL, 0.0, 0.0, eri);
+}
+
 /* 1 if the quartet (ab|cd) is screened out */
 static int or_screened(const or_jk_setup *S, int a, int b, int c, int d) {
   int ns = S->X.B->nshell;
@@ -639,7 +675,8 @@ static int or_screened(const or_jk_setup *S, int a, int b, int c, int d) {
 
 /*
  * Full J and K.  mode: 0 none, 1 Schwarz (G_ab G_cd < tau), 2 Schwarz x
- * six-block density max.  eps_p > 0 enables primitive-pair pruning.
+ * six-block density max.  eps_p > 0 enables primitive-pair pruning and (mode
+ * 2) primitive-quartet screening.
  * symmetric != 0 loops over unique quartets with explicit 8-fold scatter,
  * otherwise over all ordered quartets (N^4 reference used to validate the
  * scatter on small cases).  Returns 0 on success.
@@ -695,7 +732,7 @@ static int or_jk_impl(int nshell, const double *center, const int32_t *l, const 
             nd = off[d + 1] - off[d];
         if (S.G[(size_t)a * ns + b] * S.G[(size_t)c * ns + d] >= tau) cnt += (double)na * nb * nc * nd;
         if (or_screened(&S, a, b, c, d)) continue;
-        or_shell_quartet(&S.X, &w, a, b, c, d, -1, -1, eri);
+        or_jk_quartet(&S, &w, a, b, c, d, eps_p, eri);
         for (int i = 0; i < na; ++i)
           for (int j = 0; j < nb; ++j)
             for (int k = 0; k < nc; ++k)
@@ -815,7 +852,7 @@ int oracle_jk_blocks(int nshell, const double *center, const int32_t *l, const i
         for (int d = 0; d < ns; ++d) {
           int nc = OR_NC(l[c]), nd = OR_NC(l[d]);
           if (!or_screened(&S, a, b, c, d)) {
-            or_shell_quartet(&S.X, &w, a, b, c, d, -1, -1, eri);
+            or_jk_quartet(&S, &w, a, b, c, d, eps_p, eri);
             for (int i = 0; i < na; ++i)
               for (int j = 0; j < nb; ++j)
                 for (int p = 0; p < nc; ++p)
@@ -825,7 +862,7 @@ int oracle_jk_blocks(int nshell, const double *center, const int32_t *l, const i
           }
           if (!or_screened(&S, a, c, b, d)) {
             /* (a c | b d): K_ij += (i p | j q) D_pq */
-            or_shell_quartet(&S.X, &w, a, c, b, d, -1, -1, eri);
+            or_jk_quartet(&S, &w, a, c, b, d, eps_p, eri);
             for (int i = 0; i < na; ++i)
               for (int p = 0; p < nc; ++p)
                 for (int j = 0; j < nb; ++j)

@@ -457,3 +457,74 @@ def test_bf16_rounding_reference():
     # bfloat16 keeps 8 significant bits: relative rounding error <= 2^-9
     assert np.all(np.abs(r - x) <= np.abs(x) * 2.0 ** -8)
     assert r[0] == 1.0 and r[1] == 1.0  # 1 + 2^-8 is a tie that rounds to even
+
+
+def test_primitive_quartet_screening_brute_force():
+    """The primitive-level rules, written out independently over s shells
+    from primitive integrals (pinned above by quadrature) and normalised
+    coefficients (pinned by the overlap diagonal): a primitive pair [ab] is
+    dropped iff G_[ab] Gmax < tau eps, and inside a contracted quartet that
+    passes the six-block test a primitive quartet is skipped iff
+    G_[ab] G_[cd] Dmax < tau eps (Sec. 3.2 primitive Cauchy-Schwarz bound at
+    the level of primitive integrals, Sec. 3.3)."""
+    r = np.random.Generator(np.random.PCG64(41))
+    bas = molgen.random_shells(r, [0, 0, 0, 0, 0], spread=2.5, kmax=3)
+    ns = len(bas["l"])
+    D = r.uniform(-1, 1, (ns, ns))
+    D = D + D.T
+    cn = oracle.norm_coefs(bas)
+    ctr, po, npr, ex = bas["center"].reshape(-1, 3), bas["prim_off"], bas["nprim"], bas["exps"]
+
+    def prims(s):
+        return [(ex[po[s] + i], cn[po[s] + i]) for i in range(npr[s])]
+
+    def pe(a, b, c, d, pa, pb, pc, pd):
+        (ea, ca), (eb, cb), (ec, cc), (ed, cd) = pa, pb, pc, pd
+        return ca * cb * cc * cd * oracle.prim_eri(0, 0, 0, 0, ea, ctr[a], eb, ctr[b], ec, ctr[c], ed, ctr[d])[0, 0, 0, 0]
+
+    Gp = {}
+    for a in range(ns):
+        for b in range(ns):
+            Gp[a, b] = np.array([[np.sqrt(abs(pe(a, b, a, b, pa, pb, pa, pb))) for pb in prims(b)] for pa in prims(a)])
+    G = np.array([[np.sqrt(abs(sum(pe(a, b, a, b, pa, pb, pc, pd) for pa in prims(a) for pb in prims(b)
+                                   for pc in prims(a) for pd in prims(b)))) for b in range(ns)] for a in range(ns)])
+    gmax = G.max()
+    Dabs = np.abs(D)
+    for tau, eps in ((1e-3, 1e-2), (3e-3, 0.5)):
+        thr = tau * eps
+        nskip = 0
+
+        def eri(a, b, c, d):
+            nonlocal nskip
+            g = G[a, b] * G[c, d]
+            dm = max(Dabs[a, b], Dabs[c, d], Dabs[a, c], Dabs[a, d], Dabs[b, c], Dabs[b, d])
+            if g < tau or g * dm < tau:
+                return 0.0
+            v = 0.0
+            for i, pa in enumerate(prims(a)):
+                for j, pb in enumerate(prims(b)):
+                    if Gp[a, b][i, j] * gmax < thr:
+                        continue
+                    for k, pc in enumerate(prims(c)):
+                        for m, pd in enumerate(prims(d)):
+                            if Gp[c, d][k, m] * gmax < thr:
+                                continue
+                            if Gp[a, b][i, j] * Gp[c, d][k, m] * dm < thr:
+                                nskip += 1
+                                continue
+                            v += pe(a, b, c, d, pa, pb, pc, pd)
+            return v
+
+        Jr = np.zeros((ns, ns))
+        Kr = np.zeros((ns, ns))
+        for a in range(ns):
+            for b in range(ns):
+                for c in range(ns):
+                    for d in range(ns):
+                        Jr[a, b] += eri(a, b, c, d) * D[c, d]
+                        Kr[a, b] += eri(a, c, b, d) * D[c, d]
+        J, K = oracle.jk(bas, D, tau=tau, mode=oracle.SCREEN_DENSITY, eps_prune=eps)
+        assert nskip > 0
+        assert np.abs(J - Jr).max() < 1e-12 and np.abs(K - Kr).max() < 1e-12
+        J0, K0 = oracle.jk(bas, D, tau=tau, mode=oracle.SCREEN_DENSITY, eps_prune=0.0)
+        assert np.abs(J - J0).max() > 0
