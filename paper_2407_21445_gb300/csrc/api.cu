@@ -160,6 +160,8 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   const size_t o_U = pk.add(st.U.data(), st.U.size() * sizeof(double));
   const size_t o_eoff = pk.add(st.eoff.data(), st.eoff.size() * sizeof(int));
   const size_t o_E = pk.add(st.E.data(), st.E.size() * sizeof(double));
+  const size_t o_Gp = pk.add(st.Gp.data(), st.Gp.size() * sizeof(double));
+  const size_t o_Gpf = pk.add(st.Gpf.data(), st.Gpf.size() * sizeof(float));
   const size_t o_Gf = pk.add(st.Gf.data(), st.Gf.size() * sizeof(float));
   const size_t o_shl = pk.add(st.shl.data(), st.shl.size() * sizeof(float));
   const size_t o_paf = pk.add(st.paf.data(), st.paf.size() * sizeof(float4));
@@ -191,6 +193,8 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   dp.U = (const double *)(d + o_U);
   dp.eoff = (const int *)(d + o_eoff);
   dp.E = (const double *)(d + o_E);
+  dp.Gp = st.Gp.empty() ? nullptr : (const double *)(d + o_Gp);
+  dp.Gpf = st.Gpf.empty() ? nullptr : (const float *)(d + o_Gpf);
   dp.paf = (const float4 *)(d + o_paf);
   dp.Gf = (const float *)(d + o_Gf);
   dp.smol = st.smol.empty() ? nullptr : (const int *)(d + o_smol);
@@ -442,6 +446,10 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     for (int i = pr.x; i < pr.x + pr.y; ++i)
       if (!(o.prune_eps > 0.0 && Gprim[i] * gmax < tau * o.prune_eps)) kept_prims[P].push_back(i);
     if (kept_prims[P].empty()) continue;
+    // strongest primitive pairs first, so that the primitive-quartet test can
+    // end a primitive loop at its first skip (Sec. 3.2 ordering by G_[ab])
+    std::stable_sort(kept_prims[P].begin(), kept_prims[P].end(),
+                     [&Gprim](int x, int y) { return Gprim[x] > Gprim[y]; });
     const int nk = (int)kept_prims[P].size();
     keep.push_back({P, all.cls[P], nk, bucket_of(nk), Gpair[P]});
   }
@@ -464,6 +472,8 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
       st.paf.push_back(all.paf[i]);
       st.U.push_back(all.U[i]);
       st.Uf.push_back((float)all.U[i]);
+      st.Gp.push_back(Gprim[i]);
+      st.Gpf.push_back((float)Gprim[i]);
       st.eoff.push_back((int)st.E.size());
       const int n = ct.nE[all.cls[P]];
       st.E.insert(st.E.end(), all.E.begin() + all.eoff[i], all.E.begin() + all.eoff[i] + n);
@@ -687,8 +697,8 @@ fock_status build_jk_events(const fock_shellpairs *sp, const double *D, double s
     where = tier_name;
     if (ev) e = cudaEventRecord(ev[t], stream);
     if (e == cudaSuccess)
-      e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, J, K, counters + t, stream, Df,
-                         sp->opts.fp32_cutoff, Dshf);
+      e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, sp->prune_eps, J, K, counters + t, stream,
+                         Df, sp->opts.fp32_cutoff, Dshf);
     if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
   }
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[nt], stream);
@@ -756,10 +766,24 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
       if (g * dm < tau) continue;
       q2 += 1;
       e2 += ne;
-      const double np = (double)sp->h_prim[P].y * sp->h_prim[Q].y;
+      // primitive quartets the kernels evaluate (same skip rule and order)
+      const int2 pb = sp->h_prim[P], pk = sp->h_prim[Q];
+      const double *Gp = sp->host.Gp.data();
+      const double teps = sp->prune_eps > 0.0 ? tau * sp->prune_eps : 0.0;
+      double np = 0.0, nbra = 0.0;
+      for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
+        int n = 0;
+        for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
+          if (Gp[ip] * Gp[jq] * dm < teps) break;
+          ++n;
+        }
+        if (n == 0) break;
+        np += n;
+        nbra += 1;
+      }
       pq += np;
       const FlopTable &ft = flop_table();
-      const double f = np * ft.prim[sp->h_cls[P]][sp->h_cls[Q]] + sp->h_prim[P].y * ft.bra[sp->h_cls[P]][sp->h_cls[Q]] +
+      const double f = np * ft.prim[sp->h_cls[P]][sp->h_cls[Q]] + nbra * ft.bra[sp->h_cls[P]][sp->h_cls[Q]] +
                        12.0 * ne;
       fl += f;
       if (mixed && g * dm < sp->opts.fp32_cutoff) {

@@ -33,6 +33,7 @@ struct BatchPlan {
   int device = 0, nmol = 0;
   bool mixed = false;
   double cutoff = 0.0;
+  double prim_eps = 0.0;  // primitive-quartet screening factor (prune_eps)
   DevPairs dev{};
   void *d_block = nullptr;
   std::vector<Tier> tiers;
@@ -87,6 +88,7 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
   bp->device = bases[0]->device;
   bp->mixed = bases[0]->opts.precision == FOCK_MIXED && bases[0]->opts.fp32_cutoff > 0.0;
   bp->cutoff = bases[0]->opts.fp32_cutoff;
+  bp->prim_eps = bases[0]->prune_eps;
   Staging m;
   struct Key {
     int cb, ck, G, sb, tag;
@@ -128,6 +130,8 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
     m.pf.insert(m.pf.end(), h.pf.begin(), h.pf.end());
     m.paf.insert(m.paf.end(), h.paf.begin(), h.paf.end());
     m.U.insert(m.U.end(), h.U.begin(), h.U.end());
+    m.Gp.insert(m.Gp.end(), h.Gp.begin(), h.Gp.end());
+    m.Gpf.insert(m.Gpf.end(), h.Gpf.begin(), h.Gpf.end());
     m.Uf.insert(m.Uf.end(), h.Uf.begin(), h.Uf.end());
     for (int o : h.eoff) m.eoff.push_back(o + (int)evals);
     m.E.insert(m.E.end(), h.E.begin(), h.E.end());
@@ -259,8 +263,8 @@ cudaError_t enqueue(BatchPlan *bp, double tau, const cudaEvent_t *ev = nullptr) 
   for (size_t t = 0; t < bp->tiers.size() && e == cudaSuccess; ++t) {
     if (ev) e = cudaEventRecord(ev[t], st);
     if (e == cudaSuccess)
-      e = launch_jk_tier_batch(bp->tiers[t], bp->dev, bp->d_mt, bp->Dsh, bp->Dshf, tau, bp->counters + t, st,
-                               bp->mixed ? bp->cutoff : 0.0);
+      e = launch_jk_tier_batch(bp->tiers[t], bp->dev, bp->d_mt, bp->Dsh, bp->Dshf, tau, bp->prim_eps,
+                               bp->counters + t, st, bp->mixed ? bp->cutoff : 0.0);
   }
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[bp->tiers.size()], st);
   if (e == cudaSuccess) e = launch_symmetrize_batch(bp->d_mt, bp->d_n2p, bp->nmol, bp->n2_total, st);

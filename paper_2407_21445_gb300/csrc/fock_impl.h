@@ -82,6 +82,8 @@ struct DevPairs {
   const double *U;     // U_P sqrt(zeta) (2/sqrt(pi))^(1/2): pref = U_P U_Q / sqrt(zeta + eta)
   const int *eoff;     // offset of the primitive pair's E block
   const double *E;     // Hermite coefficients (Cartesian normalisation folded in)
+  const double *Gp;    // primitive Schwarz factor G_[ab]; each pair's primitives sorted by it, descending
+  const float *Gpf;    // the same rounded to FP32
   // FP32 copies for the mixed-precision path and the FP32 screening pre-test
   const float *Gf;     // G_ab rounded to FP32
   const float *shl;    // shell centres as FP32 hi/lo pairs: [6*s] = hx hy hz lx ly lz
@@ -118,6 +120,8 @@ struct Staging {
   std::vector<double> U;
   std::vector<int> eoff;
   std::vector<double> E;
+  std::vector<double> Gp;
+  std::vector<float> Gpf;
   std::vector<float4> paf;
   std::vector<float> Uf, Ef, Gf, shl;
   std::vector<int> smol;
@@ -185,8 +189,9 @@ const ClassTables *dev_class_tables();
 cudaError_t launch_schwarz(const DevPairs &dp, double *Gpair, double *Gprim, cudaStream_t st);
 cudaError_t launch_dprep(const double *D, int nbf, const int *sbf, const int *sl, int nshell,
                          double *Dsh, cudaStream_t st, float *Df = nullptr, float *Dshf = nullptr);
+// prim_eps: primitive-quartet screening factor (the handle's prune_eps; 0 = off)
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh,
-                           double tau, double *J, double *K, int *counter, cudaStream_t st,
+                           double tau, double prim_eps, double *J, double *K, int *counter, cudaStream_t st,
                            const float *Df = nullptr, double fp32_cutoff = 0.0, const float *Dshf = nullptr);
 cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st);
 // batched variants (one launch over every molecule of a batch)
@@ -197,7 +202,7 @@ cudaError_t launch_dprep_batch(const MolEntry *mt, const long long *dsh_prefix, 
 cudaError_t launch_symmetrize_batch(const MolEntry *mt, const long long *n2_prefix, int nmol, long long total,
                                     cudaStream_t st);
 cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEntry *mt, const double *Dsh,
-                                 const float *Dshf, double tau, int *counter, cudaStream_t st,
+                                 const float *Dshf, double tau, double prim_eps, int *counter, cudaStream_t st,
                                  double fp32_cutoff);
 cudaError_t configure_tier(Tier &t);
 int read_and_clear_status(cudaStream_t st, int *status);

@@ -28,6 +28,9 @@ struct KArgs {
   float tau_lo, tau_hi;  // tau (1 -+ 1e-4): FP32 decisions outside this band are exact
   float fp32_cutoff_f;   // fp32_cutoff rounded to FP32
   const MolEntry *mt;  // batched build: per-molecule table (null for one molecule)
+  // primitive-quartet screening: [ab|cd] skipped iff G_[ab] G_[cd] Dmax < tau_eps
+  double tau_eps;      // tau * prune_eps (0 = off)
+  float tau_eps_f;
 };
 
 // The molecule a quartet belongs to: its D, J, K, dimension and the block of
@@ -106,6 +109,72 @@ __device__ __forceinline__ float quartet_bound(const KArgs &a, const MolView &mv
   dm = fmax(dm, Ds[sB * ns + sD]);
   const double b = g * dm;
   return (g < a.tau || b < a.tau) ? -1.0f : (float)b;
+}
+
+// Primitive-quartet screening inside a contracted quartet that passed
+// (Sec. 3.2 primitive Cauchy-Schwarz bound, applied to primitive integrals as
+// in the MMD scheme of Sec. 3.3): [ab|cd] is skipped iff
+// G_[ab] G_[cd] Dmax < tau * prune_eps, Dmax the six-block maximum of the
+// quartet.  The test runs on the FP32 units against a band of 1e-4
+// (relative) around the threshold; inside the band it is taken in FP64, so
+// that it always equals the FP64 decision.  Each pair's primitives are
+// sorted by G_[ab] (descending), so a skip ends the primitive loop.
+struct PrimScreen {
+  float lo, hi;  // FP32 band on G_[ab] G_[cd]
+  int sA, sB, sC, sD;  // molecule-local shells (FP64 Dmax inside the band)
+};
+
+__device__ __forceinline__ PrimScreen prim_screen(const KArgs &a, const MolView &mv, int sA, int sB, int sC,
+                                                  int sD) {
+  PrimScreen ps;
+  ps.sA = sA - mv.s0;
+  ps.sB = sB - mv.s0;
+  ps.sC = sC - mv.s0;
+  ps.sD = sD - mv.s0;
+  if (a.tau_eps <= 0.0) {
+    ps.lo = ps.hi = -1.0f;
+    return ps;
+  }
+  const int ns = mv.ns;
+  float dm;
+  if (mv.Dshf) {
+    const float *Ds = mv.Dshf;
+    dm = Ds[ps.sA * ns + ps.sB];
+    dm = fmaxf(dm, Ds[ps.sC * ns + ps.sD]);
+    dm = fmaxf(dm, Ds[ps.sA * ns + ps.sC]);
+    dm = fmaxf(dm, Ds[ps.sA * ns + ps.sD]);
+    dm = fmaxf(dm, Ds[ps.sB * ns + ps.sC]);
+    dm = fmaxf(dm, Ds[ps.sB * ns + ps.sD]);
+  } else {
+    const double *Ds = mv.Dsh;
+    double d = Ds[ps.sA * ns + ps.sB];
+    d = fmax(d, Ds[ps.sC * ns + ps.sD]);
+    d = fmax(d, Ds[ps.sA * ns + ps.sC]);
+    d = fmax(d, Ds[ps.sA * ns + ps.sD]);
+    d = fmax(d, Ds[ps.sB * ns + ps.sC]);
+    d = fmax(d, Ds[ps.sB * ns + ps.sD]);
+    dm = (float)d;
+  }
+  const float t = a.tau_eps_f / dm;
+  ps.lo = t * (1.0f - 1e-4f);
+  ps.hi = t * (1.0f + 1e-4f);
+  return ps;
+}
+
+// true = skip primitive quartet (ip | jq)
+__device__ __forceinline__ bool prim_skip(const KArgs &a, const MolView &mv, const PrimScreen &ps, int ip, int jq) {
+  const float x = a.dp.Gpf[ip] * a.dp.Gpf[jq];
+  if (x < ps.lo) return true;
+  if (x > ps.hi || ps.lo < 0.0f) return false;
+  const int ns = mv.ns;
+  const double *Ds = mv.Dsh;
+  double d = Ds[ps.sA * ns + ps.sB];
+  d = fmax(d, Ds[ps.sC * ns + ps.sD]);
+  d = fmax(d, Ds[ps.sA * ns + ps.sC]);
+  d = fmax(d, Ds[ps.sA * ns + ps.sD]);
+  d = fmax(d, Ds[ps.sB * ns + ps.sC]);
+  d = fmax(d, Ds[ps.sB * ns + ps.sD]);
+  return a.dp.Gp[ip] * a.dp.Gp[jq] * d < a.tau_eps;
 }
 
 // Density-weighted Schwarz test of quartet (P|Q) (Sec. 3.2): true = skip.

@@ -183,10 +183,15 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
 
   for (int i = gl; i < nab * ncd; i += G) eri[i] = Real(0);
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
+  // primitive-quartet screening; the decision is the same on every lane of
+  // the group, so the group leaves its loops together
+  const PrimScreen ps = prim_screen(a, mv, sA, sB, sC, sD);
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
+    if (prim_skip(a, mv, ps, ip, pk.x)) break;
     const Real *EP = Epool + dp.eoff[ip];
     for (int i = gl; i < nhab * ncd; i += G) Yh[i] = Real(0);
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
+      if (prim_skip(a, mv, ps, ip, jq)) break;
       const Real *EQ = Epool + dp.eoff[jq];
       Real X, Y, Z;
       if constexpr (F32) {
@@ -706,14 +711,16 @@ static cudaError_t set_group_smem(const Tier &t) {
   return cudaErrorInvalidValue;
 }
 
-static void set_screen_args(KArgs &a, double tau, const float *Dshf) {
+static void set_screen_args(KArgs &a, double tau, const float *Dshf, double prim_eps) {
   a.Dshf = Dshf;
   a.tau_lo = (float)(tau * (1.0 - 1e-4));
   a.tau_hi = (float)(tau * (1.0 + 1e-4));
+  a.tau_eps = prim_eps > 0.0 ? tau * prim_eps : 0.0;
+  a.tau_eps_f = (float)a.tau_eps;
 }
 
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh, double tau,
-                           double *J, double *K, int *counter, cudaStream_t st, const float *Df,
+                           double prim_eps, double *J, double *K, int *counter, cudaStream_t st, const float *Df,
                            double fp32_cutoff, const float *Dshf) {
   if (t.nunits == 0) return cudaSuccess;
   if (t.reg_cb >= 0) {
@@ -737,7 +744,7 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
     a.fp32_cutoff_f = (float)a.fp32_cutoff;
     a.Df = Df;
     a.boysf = dev_boys_f();
-    set_screen_args(a, tau, Dshf);
+    set_screen_args(a, tau, Dshf, prim_eps);
     cudaError_t e = launch_reg_a(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
     if (e == cudaErrorInvalidValue) e = launch_reg_b(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
     if (e == cudaErrorInvalidValue) e = launch_reg_c(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
@@ -766,7 +773,7 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
   a.fp32_cutoff_f = (float)a.fp32_cutoff;
   a.Df = Df;
   a.boysf = dev_boys_f();
-  set_screen_args(a, tau, Dshf);
+  set_screen_args(a, tau, Dshf, prim_eps);
   const dim3 blk(32 * t.warps_per_block);
   switch (t.G) {
     case 1: k_jk<1><<<t.blocks, blk, t.smem, st>>>(a); break;
@@ -782,7 +789,8 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
 
 // One tier of a batched build: same kernels, per-molecule D/J/K from mt.
 cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEntry *mt, const double *Dsh,
-                                 const float *Dshf, double tau, int *counter, cudaStream_t st, double fp32_cutoff) {
+                                 const float *Dshf, double tau, double prim_eps, int *counter, cudaStream_t st,
+                                 double fp32_cutoff) {
   if (t.nunits == 0) return cudaSuccess;
   KArgs a;
   memset(&a, 0, sizeof(a));
@@ -801,7 +809,7 @@ cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEnt
   a.mt = mt;
   a.fp32_cutoff = fp32_cutoff;
   a.fp32_cutoff_f = (float)a.fp32_cutoff;
-  set_screen_args(a, tau, Dshf);
+  set_screen_args(a, tau, Dshf, prim_eps);
   const int threads = 32 * t.warps_per_block;
   if (t.reg_cb >= 0) {
     cudaError_t e = launch_reg_a(t.reg_cb, t.reg_ck, a, t.blocks, threads, st);

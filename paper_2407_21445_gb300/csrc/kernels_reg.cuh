@@ -132,13 +132,16 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &m
   };
   sfor<NAB * NCD>([&](auto i) { eri_at(FK_CI(i)) = 0.0; });
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
+  const PrimScreen ps = prim_screen(a, mv, sA, sB, sC, sD);
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
+    if (prim_skip(a, mv, ps, ip, pk.x)) break;  // weaker bra primitives follow
     const PZ P4 = dp.pz[ip];
     const float4 Pf = dp.pf[ip];
     const double UsP = dp.U[ip];
     double Y[NHAB * NCD];
     sfor<NHAB * NCD>([&](auto i) { Y[FK_CI(i)] = 0.0; });
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
+      if (prim_skip(a, mv, ps, ip, jq)) break;  // weaker ket primitives follow
       const PrimQuartet q = prim_quartet(P4, Pf, UsP, dp.pz[jq], dp.pf[jq], dp.U[jq]);
       double F[L + 1];
       boys_seeds<L>(a.boys, q, F);
@@ -256,12 +259,15 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
   float eri[NAB * NCD];
   sfor<NAB * NCD>([&](auto i) { eri[FK_CI(i)] = 0.0f; });
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
+  const PrimScreen ps = prim_screen(a, mv, sA, sB, sC, sD);
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
+    if (prim_skip(a, mv, ps, ip, pk.x)) break;
     const float4 PA = dp.paf[ip];
     const float UP = dp.Uf[ip];
     float Y[NHAB * NCD];
     sfor<NHAB * NCD>([&](auto i) { Y[FK_CI(i)] = 0.0f; });
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
+      if (prim_skip(a, mv, ps, ip, jq)) break;
       const float4 QC = dp.paf[jq];
       const float X = PA.x - QC.x + ACx, Yd = PA.y - QC.y + ACy, Z = PA.z - QC.z + ACz;
       const float rs = rsqrtf(PA.w + QC.w);
