@@ -71,6 +71,14 @@ __device__ __forceinline__ void group_sync(unsigned mask, int G) {
 __constant__ double c_small[16] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15};
 __constant__ float c_smallf[16] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15};
 
+// x with its sign flipped when s == 1 (integer units only)
+__device__ __forceinline__ double neg_if(double x, int s) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)s << 63));
+}
+__device__ __forceinline__ float neg_if(float x, int s) {
+  return __int_as_float(__float_as_int(x) ^ (s << 31));
+}
+
 template <class Real>
 __device__ __forceinline__ Real small_int(int i) {
   if constexpr (sizeof(Real) == 8)
@@ -221,15 +229,24 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
         const uint8_t *cc = ct.comp[lc][ic], *dd = ct.comp[ld][id];
         const int Tx = cc[0] + dd[0], Ty = cc[1] + dd[1], Tz = cc[2] + dd[2];
         const Real *Eq = EQ + ct.eoff[ck][kc];
-        Real acc = Yh[it];
+        // two independent accumulation chains (even / odd v) for latency
+        Real acc0 = Yh[it], acc1 = Real(0);
         int e = 0;
         for (int t = 0; t <= Tx; ++t)
-          for (int u = 0; u <= Ty; ++u)
-            for (int v = 0; v <= Tz; ++v, ++e) {
-              const Real r = R[hidx(tp + t, up + u, vp + v)];
-              acc = ((t + u + v) & 1) ? fma(-Eq[e], r, acc) : fma(Eq[e], r, acc);
+          for (int u = 0; u <= Ty; ++u) {
+            const int s = (t + u) & 1;  // (-1)^(t+u+v): s for even v, flipped for odd v
+            int v = 0;
+            for (; v < Tz; v += 2, e += 2) {
+              const Real r0 = R[hidx(tp + t, up + u, vp + v)], r1 = R[hidx(tp + t, up + u, vp + v + 1)];
+              acc0 = fma(neg_if(Eq[e], s), r0, acc0);
+              acc1 = fma(neg_if(Eq[e + 1], s ^ 1), r1, acc1);
             }
-        Yh[it] = acc;
+            if (v == Tz) {
+              acc0 = fma(neg_if(Eq[e], s), R[hidx(tp + t, up + u, vp + v)], acc0);
+              ++e;
+            }
+          }
+        Yh[it] = acc0 + acc1;
       }
       group_sync(gmask, G);
     }
@@ -240,12 +257,21 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
       const uint8_t *ac = ct.comp[la][ia], *bc = ct.comp[lb][ib];
       const int Tx = ac[0] + bc[0], Ty = ac[1] + bc[1], Tz = ac[2] + bc[2];
       const Real *Ep = EP + ct.eoff[cb][ka];
-      Real acc = eri[it];
+      Real acc0 = eri[it], acc1 = Real(0);
       int e = 0;
       for (int t = 0; t <= Tx; ++t)
-        for (int u = 0; u <= Ty; ++u)
-          for (int v = 0; v <= Tz; ++v, ++e) acc = fma(Ep[e], Yh[hidx(t, u, v) * ncd + kc], acc);
-      eri[it] = acc;
+        for (int u = 0; u <= Ty; ++u) {
+          int v = 0;
+          for (; v < Tz; v += 2, e += 2) {
+            acc0 = fma(Ep[e], Yh[hidx(t, u, v) * ncd + kc], acc0);
+            acc1 = fma(Ep[e + 1], Yh[hidx(t, u, v + 1) * ncd + kc], acc1);
+          }
+          if (v == Tz) {
+            acc0 = fma(Ep[e], Yh[hidx(t, u, v) * ncd + kc], acc0);
+            ++e;
+          }
+        }
+      eri[it] = acc0 + acc1;
     }
     group_sync(gmask, G);
   }
@@ -266,48 +292,78 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
   const Real fac2 = Real(2) * fac;
   const int n1 = nab, n2 = n1 + ncd, n3 = n2 + na * nc, n4 = n3 + na * nd, n5 = n4 + nb * nc,
             n6 = n5 + nb * nd;
+  // sum_m x(m) y(m) over two independent chains (even / odd m)
+  auto dot2 = [](int n, auto &&xy) -> Real {
+    Real s0 = Real(0), s1 = Real(0), x, y;
+    int m = 0;
+    for (; m + 1 < n; m += 2) {
+      xy(m, x, y);
+      s0 = fma(x, y, s0);
+      xy(m + 1, x, y);
+      s1 = fma(x, y, s1);
+    }
+    if (m < n) {
+      xy(m, x, y);
+      s0 = fma(x, y, s0);
+    }
+    return s0 + s1;
+  };
   for (int o = gl; o < n6; o += G) {
-    Real s = Real(0);
+    Real s;
     double *dst;
-    if (o < n1) {
+    if (o < n1) {  // J_ab += (ab|cd) D_cd
       const int ia = o / nb, ib = o - ia * nb;
       const Real *e = eri + (size_t)o * ncd;
-      for (int ic = 0; ic < nc; ++ic)
-        for (int id = 0; id < nd; ++id) s = fma(e[ic * nd + id], Dm[(size_t)(fc + ic) * N + fd + id], s);
+      s = dot2(ncd, [&](int m, Real &x, Real &y) {
+        const int ic = m / nd, id = m - ic * nd;
+        x = e[m];
+        y = Dm[(size_t)(fc + ic) * N + fd + id];
+      });
       dst = mv.J + (size_t)(fa + ia) * N + fb + ib;
       s *= fac2;
-    } else if (o < n2) {
+    } else if (o < n2) {  // J_cd += (ab|cd) D_ab
       const int k = o - n1, ic = k / nd, id = k - ic * nd;
-      for (int ia = 0; ia < na; ++ia)
-        for (int ib = 0; ib < nb; ++ib) s = fma(eri[(ia * nb + ib) * ncd + k], Dm[(size_t)(fa + ia) * N + fb + ib], s);
+      s = dot2(nab, [&](int m, Real &x, Real &y) {
+        const int ia = m / nb, ib = m - ia * nb;
+        x = eri[(size_t)m * ncd + k];
+        y = Dm[(size_t)(fa + ia) * N + fb + ib];
+      });
       dst = mv.J + (size_t)(fc + ic) * N + fd + id;
       s *= fac2;
     } else if (o < n3) {  // K_ac += (ab|cd) D_bd
       const int k = o - n2, ia = k / nc, ic = k - ia * nc;
-      for (int ib = 0; ib < nb; ++ib)
-        for (int id = 0; id < nd; ++id)
-          s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fb + ib) * N + fd + id], s);
+      s = dot2(nb * nd, [&](int m, Real &x, Real &y) {
+        const int ib = m / nd, id = m - ib * nd;
+        x = eri[((ia * nb + ib) * nc + ic) * nd + id];
+        y = Dm[(size_t)(fb + ib) * N + fd + id];
+      });
       dst = mv.K + (size_t)(fa + ia) * N + fc + ic;
       s *= fac;
     } else if (o < n4) {  // K_ad += (ab|cd) D_bc
       const int k = o - n3, ia = k / nd, id = k - ia * nd;
-      for (int ib = 0; ib < nb; ++ib)
-        for (int ic = 0; ic < nc; ++ic)
-          s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fb + ib) * N + fc + ic], s);
+      s = dot2(nb * nc, [&](int m, Real &x, Real &y) {
+        const int ib = m / nc, ic = m - ib * nc;
+        x = eri[((ia * nb + ib) * nc + ic) * nd + id];
+        y = Dm[(size_t)(fb + ib) * N + fc + ic];
+      });
       dst = mv.K + (size_t)(fa + ia) * N + fd + id;
       s *= fac;
     } else if (o < n5) {  // K_bc += (ab|cd) D_ad
       const int k = o - n4, ib = k / nc, ic = k - ib * nc;
-      for (int ia = 0; ia < na; ++ia)
-        for (int id = 0; id < nd; ++id)
-          s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fa + ia) * N + fd + id], s);
+      s = dot2(na * nd, [&](int m, Real &x, Real &y) {
+        const int ia = m / nd, id = m - ia * nd;
+        x = eri[((ia * nb + ib) * nc + ic) * nd + id];
+        y = Dm[(size_t)(fa + ia) * N + fd + id];
+      });
       dst = mv.K + (size_t)(fb + ib) * N + fc + ic;
       s *= fac;
     } else {  // K_bd += (ab|cd) D_ac
       const int k = o - n5, ib = k / nd, id = k - ib * nd;
-      for (int ia = 0; ia < na; ++ia)
-        for (int ic = 0; ic < nc; ++ic)
-          s = fma(eri[((ia * nb + ib) * nc + ic) * nd + id], Dm[(size_t)(fa + ia) * N + fc + ic], s);
+      s = dot2(na * nc, [&](int m, Real &x, Real &y) {
+        const int ia = m / nc, ic = m - ia * nc;
+        x = eri[((ia * nb + ib) * nc + ic) * nd + id];
+        y = Dm[(size_t)(fa + ia) * N + fc + ic];
+      });
       dst = mv.K + (size_t)(fb + ib) * N + fd + id;
       s *= fac;
     }
@@ -349,11 +405,58 @@ __global__ void __launch_bounds__(128) k_jk(KArgs a) {
   const int grp = lane / G, gl = lane - grp * G;
   double *scr = scr_base + (size_t)(warp * NG + grp) * a.stride;
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+  // Warp-level work queues, as in the register kernels: the unit's kets are
+  // screened 32 at a time and the survivors appended to an FP64 or an FP32
+  // queue; the queues are drained NG quartets at a time (one per group), so
+  // the groups of a warp run the same precision and none holds a screened
+  // quartet.
+  __shared__ int queues[4][2][64];
+  int *q64 = queues[warp][0], *q32 = queues[warp][1];
+  const unsigned lt = (1u << lane) - 1u;
+  auto drain = [&](int *q, int &n, bool fp32, const MolView &mv, int P, bool all) {
+    const int k = all ? n : (n / NG) * NG;
+    for (int i = 0; i < k; i += NG)
+      if (i + grp < k) {
+        if (fp32)
+          quartet_body<G, float>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
+        else
+          quartet_body<G, double>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
+      }
+    __syncwarp();
+    const int rest = n - k;  // < NG <= 32 entries move to the front
+    const int v = lane < rest ? q[k + lane] : 0;
+    __syncwarp();
+    if (lane < rest) q[lane] = v;
+    n = rest;
+    __syncwarp();
+  };
   for (;;) {
     const int u = next_unit(a.counter, lane);
     if (u >= a.nunits) break;
     const Unit un = a.units[u];
-    for (int Q = un.k0 + grp; Q < un.k1; Q += NG) quartet<G>(a, ct, scr, un.bra, Q, gl, gmask);
+    const int P = un.bra;
+    const int2 ab = a.dp.ab[P];
+    const MolView mv = mol_view(a, ab.x);
+    int n64 = 0, n32 = 0;
+    for (int c = un.k0; c < un.k1; c += 32) {
+      const int Q = c + lane;
+      float b = -1.0f;
+      if (Q < un.k1) {
+        const int2 cd = a.dp.ab[Q];
+        b = quartet_bound(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
+      }
+      const bool is32 = b >= 0.0f && b < a.fp32_cutoff_f, is64 = b >= 0.0f && !is32;
+      const unsigned m64 = __ballot_sync(0xffffffffu, is64), m32 = __ballot_sync(0xffffffffu, is32);
+      if (is64) q64[n64 + __popc(m64 & lt)] = Q;
+      if (is32) q32[n32 + __popc(m32 & lt)] = Q;
+      n64 += __popc(m64);
+      n32 += __popc(m32);
+      __syncwarp();
+      if (n64 >= NG) drain(q64, n64, false, mv, P, false);
+      if (n32 >= NG) drain(q32, n32, true, mv, P, false);
+    }
+    if (n64 > 0) drain(q64, n64, false, mv, P, true);
+    if (n32 > 0) drain(q32, n32, true, mv, P, true);
   }
 }
 
@@ -647,9 +750,11 @@ cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st) {
 template <int G>
 static cudaError_t configure_g(Tier &t) {
   const size_t per_warp = (size_t)(32 / G) * t.stride * sizeof(double);
+  // 227 KB per block, less the kernel's static work queues
+  const size_t limit = 227 * 1024 - sizeof(int) * 4 * 2 * 64;
   int wpb = 4;
-  while (wpb > 1 && TAB_BYTES + wpb * per_warp > 227 * 1024) --wpb;
-  if (TAB_BYTES + wpb * per_warp > 227 * 1024) return cudaErrorInvalidValue;
+  while (wpb > 1 && TAB_BYTES + wpb * per_warp > limit) --wpb;
+  if (TAB_BYTES + wpb * per_warp > limit) return cudaErrorInvalidValue;
   t.warps_per_block = wpb;
   t.smem = TAB_BYTES + wpb * per_warp;
   cudaError_t e = cudaFuncSetAttribute(k_jk<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
