@@ -747,6 +747,7 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
   const bool mixed = sp->opts.precision == FOCK_MIXED && sp->opts.fp32_cutoff > 0.0;
   for (size_t ui = 0; ui < sp->h_units.size(); ++ui) {
     const Unit &u = sp->h_units[ui];
+    const bool reg = sp->tiers[sp->h_unit_tier[ui]].reg_cb >= 0;  // only register kernels run FP32 quartets
     const int P = u.bra;
     const int2 ab = sp->h_ab[P];
     for (int Q = u.k0; Q < u.k1; ++Q) {
@@ -786,7 +787,7 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
       const double f = np * ft.prim[sp->h_cls[P]][sp->h_cls[Q]] + nbra * ft.bra[sp->h_cls[P]][sp->h_cls[Q]] +
                        12.0 * ne;
       fl += f;
-      if (mixed && g * dm < sp->opts.fp32_cutoff) {
+      if (mixed && reg && g * dm < sp->opts.fp32_cutoff) {
         q32 += 1;
         fl32 += f;
       }

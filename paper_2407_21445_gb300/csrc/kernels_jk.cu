@@ -405,23 +405,22 @@ __global__ void __launch_bounds__(128) k_jk(KArgs a) {
   const int grp = lane / G, gl = lane - grp * G;
   double *scr = scr_base + (size_t)(warp * NG + grp) * a.stride;
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
-  // Warp-level work queues, as in the register kernels: the unit's kets are
-  // screened 32 at a time and the survivors appended to an FP64 or an FP32
-  // queue; the queues are drained NG quartets at a time (one per group), so
-  // the groups of a warp run the same precision and none holds a screened
-  // quartet.
-  __shared__ int queues[4][2][64];
-  int *q64 = queues[warp][0], *q32 = queues[warp][1];
+  // Warp-level work queue, as in the register kernels: the unit's kets are
+  // screened 32 at a time and the survivors appended to a queue that is
+  // drained NG quartets at a time (one per group), so no group holds a
+  // screened quartet while the others compute.  The group kernels evaluate
+  // every quartet in FP64, also in mixed mode: they are bound by instruction
+  // issue and lane utilisation rather than by the FP64 pipe (ncu: FP64 pipe
+  // ~50 % active, ~17 of 32 lanes active per instruction), an FP32 body runs
+  // about as many instructions, and switching between the two bodies in one
+  // kernel stalled on instruction fetch.
+  __shared__ int queues[4][64];
+  int *q64 = queues[warp];
   const unsigned lt = (1u << lane) - 1u;
-  auto drain = [&](int *q, int &n, bool fp32, const MolView &mv, int P, bool all) {
+  auto drain = [&](int *q, int &n, const MolView &mv, int P, bool all) {
     const int k = all ? n : (n / NG) * NG;
     for (int i = 0; i < k; i += NG)
-      if (i + grp < k) {
-        if (fp32)
-          quartet_body<G, float>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
-        else
-          quartet_body<G, double>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
-      }
+      if (i + grp < k) quartet_body<G, double>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
     __syncwarp();
     const int rest = n - k;  // < NG <= 32 entries move to the front
     const int v = lane < rest ? q[k + lane] : 0;
@@ -437,7 +436,7 @@ __global__ void __launch_bounds__(128) k_jk(KArgs a) {
     const int P = un.bra;
     const int2 ab = a.dp.ab[P];
     const MolView mv = mol_view(a, ab.x);
-    int n64 = 0, n32 = 0;
+    int n64 = 0;
     for (int c = un.k0; c < un.k1; c += 32) {
       const int Q = c + lane;
       float b = -1.0f;
@@ -445,18 +444,14 @@ __global__ void __launch_bounds__(128) k_jk(KArgs a) {
         const int2 cd = a.dp.ab[Q];
         b = quartet_bound(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
       }
-      const bool is32 = b >= 0.0f && b < a.fp32_cutoff_f, is64 = b >= 0.0f && !is32;
-      const unsigned m64 = __ballot_sync(0xffffffffu, is64), m32 = __ballot_sync(0xffffffffu, is32);
-      if (is64) q64[n64 + __popc(m64 & lt)] = Q;
-      if (is32) q32[n32 + __popc(m32 & lt)] = Q;
+      const bool keep = b >= 0.0f;
+      const unsigned m64 = __ballot_sync(0xffffffffu, keep);
+      if (keep) q64[n64 + __popc(m64 & lt)] = Q;
       n64 += __popc(m64);
-      n32 += __popc(m32);
       __syncwarp();
-      if (n64 >= NG) drain(q64, n64, false, mv, P, false);
-      if (n32 >= NG) drain(q32, n32, true, mv, P, false);
+      if (n64 >= NG) drain(q64, n64, mv, P, false);
     }
-    if (n64 > 0) drain(q64, n64, false, mv, P, true);
-    if (n32 > 0) drain(q32, n32, true, mv, P, true);
+    if (n64 > 0) drain(q64, n64, mv, P, true);
   }
 }
 
@@ -751,7 +746,7 @@ template <int G>
 static cudaError_t configure_g(Tier &t) {
   const size_t per_warp = (size_t)(32 / G) * t.stride * sizeof(double);
   // 227 KB per block, less the kernel's static work queues
-  const size_t limit = 227 * 1024 - sizeof(int) * 4 * 2 * 64;
+  const size_t limit = 227 * 1024 - sizeof(int) * 4 * 64;
   int wpb = 4;
   while (wpb > 1 && TAB_BYTES + wpb * per_warp > limit) --wpb;
   if (TAB_BYTES + wpb * per_warp > limit) return cudaErrorInvalidValue;
@@ -874,9 +869,9 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
   a.boys = dev_boys();
   a.tabs = dev_class_tables();
   a.mt = nullptr;
-  a.fp32_cutoff = Df ? fp32_cutoff : 0.0;
-  a.fp32_cutoff_f = (float)a.fp32_cutoff;
-  a.Df = Df;
+  a.fp32_cutoff = 0.0;  // the group kernels evaluate every quartet in FP64
+  a.fp32_cutoff_f = 0.0f;
+  a.Df = nullptr;
   a.boysf = dev_boys_f();
   set_screen_args(a, tau, Dshf, prim_eps);
   const dim3 blk(32 * t.warps_per_block);
@@ -912,7 +907,7 @@ cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEnt
   a.tabs = dev_class_tables();
   a.boysf = dev_boys_f();
   a.mt = mt;
-  a.fp32_cutoff = fp32_cutoff;
+  a.fp32_cutoff = t.reg_cb >= 0 ? fp32_cutoff : 0.0;  // group kernels: FP64 only
   a.fp32_cutoff_f = (float)a.fp32_cutoff;
   set_screen_args(a, tau, Dshf, prim_eps);
   const int threads = 32 * t.warps_per_block;
