@@ -74,12 +74,18 @@ __device__ __forceinline__ PrimQuartet prim_quartet(const PZ &P4, const float4 &
 }
 
 // F_m(T) for one m from the table (Taylor about T_i, Horner in x = T_i - T).
+// The eight coefficients of an entry are 64 contiguous bytes on a 64-byte
+// boundary (the table is one device allocation), read as four 16-byte loads.
 __device__ __forceinline__ double boys_taylor(const double *__restrict__ tab, int gi, int m, double x) {
-  const double *c = tab + ((size_t)gi * (LTOT + 1) + m) * BOYS_TAYLOR;
-  double f = __ldg(c + 7);
-#pragma unroll
-  for (int k = 6; k >= 0; --k) f = fma(f, x, __ldg(c + k));
-  return f;
+  const double2 *c = reinterpret_cast<const double2 *>(tab + ((size_t)gi * (LTOT + 1) + m) * BOYS_TAYLOR);
+  const double2 c67 = __ldg(c + 3), c45 = __ldg(c + 2), c23 = __ldg(c + 1), c01 = __ldg(c);
+  double f = fma(c67.y, x, c67.x);
+  f = fma(f, x, c45.y);
+  f = fma(f, x, c45.x);
+  f = fma(f, x, c23.y);
+  f = fma(f, x, c23.x);
+  f = fma(f, x, c01.y);
+  return fma(f, x, c01.x);
 }
 
 // Seeds pref (-2 alpha)^m F_m(T), m = 0..L, into out[] (compile-time L).
@@ -182,11 +188,15 @@ __device__ __forceinline__ void boys_seeds_f32(const float *__restrict__ tab, fl
     const float x = (float)gi * (float)BOYS_H - T;
 #pragma unroll
     for (int m = 0; m <= L; ++m) {
-      const float *c = tab + ((size_t)gi * (LTOT + 1) + m) * BOYS_TAYLOR;
-      float f = __ldg(c + 5);
-#pragma unroll
-      for (int k = 4; k >= 0; --k) f = fmaf(f, x, __ldg(c + k));
-      out[m] = f;
+      // six of the entry's eight coefficients (32 bytes on a 32-byte boundary)
+      const float4 *c = reinterpret_cast<const float4 *>(tab + ((size_t)gi * (LTOT + 1) + m) * BOYS_TAYLOR);
+      const float4 c03 = __ldg(c);
+      const float2 c45 = __ldg(reinterpret_cast<const float2 *>(c + 1));
+      float f = fmaf(c45.y, x, c45.x);
+      f = fmaf(f, x, c03.w);
+      f = fmaf(f, x, c03.z);
+      f = fmaf(f, x, c03.y);
+      out[m] = fmaf(f, x, c03.x);
     }
   } else {
     const float rt = rsqrtf(T);

@@ -69,22 +69,10 @@ __device__ __forceinline__ void group_sync(unsigned mask, int G) {
 // R^{(0)}_{tuv}, t+u+v <= L, into the returned buffer (one of R0/R1).
 // F must hold base values pref (-2alpha)^n F_n(T), n = 0..L; R0[0] = F[L].
 __constant__ double c_small[16] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15};
-__constant__ float c_smallf[16] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15};
 
 // x with its sign flipped when s == 1 (integer units only)
 __device__ __forceinline__ double neg_if(double x, int s) {
   return __longlong_as_double(__double_as_longlong(x) ^ ((long long)s << 63));
-}
-__device__ __forceinline__ float neg_if(float x, int s) {
-  return __int_as_float(__float_as_int(x) ^ (s << 31));
-}
-
-template <class Real>
-__device__ __forceinline__ Real small_int(int i) {
-  if constexpr (sizeof(Real) == 8)
-    return c_small[i];
-  else
-    return c_smallf[i];
 }
 
 template <int G, class Real>
@@ -101,13 +89,13 @@ __device__ __forceinline__ Real *hermite_r(const ClassTables &ct, int L, Real X,
         int t = ct.hvec[e][0], u = ct.hvec[e][1], w = ct.hvec[e][2];
         if (t > 0) {
           v = X * cur[hidx(t - 1, u, w)];
-          if (t > 1) v = fma(small_int<Real>(t - 1), cur[hidx(t - 2, u, w)], v);
+          if (t > 1) v = fma(c_small[t - 1], cur[hidx(t - 2, u, w)], v);
         } else if (u > 0) {
           v = Y * cur[hidx(t, u - 1, w)];
-          if (u > 1) v = fma(small_int<Real>(u - 1), cur[hidx(t, u - 2, w)], v);
+          if (u > 1) v = fma(c_small[u - 1], cur[hidx(t, u - 2, w)], v);
         } else {
           v = Z * cur[hidx(t, u, w - 1)];
-          if (w > 1) v = fma(small_int<Real>(w - 1), cur[hidx(t, u, w - 2)], v);
+          if (w > 1) v = fma(c_small[w - 1], cur[hidx(t, u, w - 2)], v);
         }
       }
       nxt[e] = v;
@@ -120,38 +108,11 @@ __device__ __forceinline__ Real *hermite_r(const ClassTables &ct, int L, Real X,
   return cur;
 }
 
-// FP32 seeds for the group kernel (lanes over m), R0[0] = F[L].
+// One contracted quartet on a group of G lanes (FP64).
 template <int G>
-__device__ __forceinline__ void boys_seeds_rt_f32(const float *__restrict__ tab, float T, float pref, float m2a, int L,
-                                                  float *F, float *R0, int gl) {
-  for (int m = gl; m <= L; m += G) {
-    float f;
-    if (T < (float)BOYS_TMAX) {
-      const int gi = __float2int_rn(T * (float)BOYS_INVH);
-      const float x = (float)gi * (float)BOYS_H - T;
-      const float *c = tab + ((size_t)gi * (LTOT + 1) + m) * BOYS_TAYLOR;
-      f = __ldg(c + 5);
-      for (int k = 4; k >= 0; --k) f = fmaf(f, x, __ldg(c + k));
-    } else {
-      const float rt = rsqrtf(T), it = rt * rt;
-      f = 0.886226925452758f * rt;
-      for (int k = 1; k <= m; ++k) f *= ((float)k - 0.5f) * it;
-    }
-    float c = pref;
-    for (int k = 0; k < m; ++k) c *= m2a;
-    F[m] = f * c;
-    if (m == L) R0[0] = F[m];
-  }
-}
-
-// One contracted quartet on a group of G lanes, in FP64 (Real = double) or
-// in FP32 (Real = float, the mixed-precision path below the cutoff: FP32
-// table, pair-relative centres, FP32 copies of U, E and D, exact FP32->FP64
-// conversion of every digested element before the FP64 atomic add).
-template <int G, class Real>
 __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_d, int P, int Q, int gl,
                              unsigned gmask, const MolView &mv) {
-  constexpr bool F32 = sizeof(Real) == 4;
+  using Real = double;
   const DevPairs &dp = a.dp;
   const int2 ab = dp.ab[P], cd = dp.ab[Q];
   const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
@@ -176,18 +137,7 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
   Real *R0 = Yh + nhab * ncd;
   Real *R1 = R0 + nhL;
   Real *F = R1 + nhL;
-  const Real *Epool;
-  if constexpr (F32)
-    Epool = dp.Ef;
-  else
-    Epool = dp.E;
-  float ACx = 0.f, ACy = 0.f, ACz = 0.f;
-  if constexpr (F32) {
-    const float *ha = dp.shl + 6 * sA, *hc = dp.shl + 6 * sC;
-    ACx = (ha[0] - hc[0]) + (ha[3] - hc[3]);
-    ACy = (ha[1] - hc[1]) + (ha[4] - hc[4]);
-    ACz = (ha[2] - hc[2]) + (ha[5] - hc[5]);
-  }
+  const Real *Epool = dp.E;
 
   for (int i = gl; i < nab * ncd; i += G) eri[i] = Real(0);
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
@@ -201,24 +151,10 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
       if (prim_skip(a, mv, ps, ip, jq)) break;
       const Real *EQ = Epool + dp.eoff[jq];
-      Real X, Y, Z;
-      if constexpr (F32) {
-        const float4 PA = dp.paf[ip], QC = dp.paf[jq];
-        X = PA.x - QC.x + ACx;
-        Y = PA.y - QC.y + ACy;
-        Z = PA.z - QC.z + ACz;
-        const float rs = rsqrtf(PA.w + QC.w);
-        const float alpha = (PA.w * QC.w) * (rs * rs);
-        const float T = alpha * fmaf(X, X, fmaf(Y, Y, Z * Z));
-        boys_seeds_rt_f32<G>(a.boysf, T, dp.Uf[ip] * dp.Uf[jq] * rs, -2.0f * alpha, L, F, R0, gl);
-      } else {
-        const PrimQuartet q = prim_quartet(dp.pz[ip], dp.pf[ip], dp.U[ip], dp.pz[jq], dp.pf[jq], dp.U[jq]);
-        FK_CHECK(q.T >= 0.0 && q.T == q.T && q.gi <= BOYS_NGRID - 1, 9, jq);
-        X = q.X;
-        Y = q.Y;
-        Z = q.Z;
-        boys_seeds_rt<G>(a.boys, q, L, F, R0, gl);
-      }
+      const PrimQuartet q = prim_quartet(dp.pz[ip], dp.pf[ip], dp.U[ip], dp.pz[jq], dp.pf[jq], dp.U[jq]);
+      FK_CHECK(q.T >= 0.0 && q.T == q.T && q.gi <= BOYS_NGRID - 1, 9, jq);
+      const Real X = q.X, Y = q.Y, Z = q.Z;
+      boys_seeds_rt<G>(a.boys, q, L, F, R0, gl);
       group_sync(gmask, G);
       const Real *R = hermite_r<G, Real>(ct, L, X, Y, Z, F, R0, R1, gl, gmask);
       // ket transform, accumulated over ket primitives
@@ -284,11 +220,7 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
   if (P == Q) fac *= Real(0.5);
   const int N = mv.N;
   const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
-  const Real *Dm;
-  if constexpr (F32)
-    Dm = mv.Df;
-  else
-    Dm = mv.D;
+  const Real *Dm = mv.D;
   const Real fac2 = Real(2) * fac;
   const int n1 = nab, n2 = n1 + ncd, n3 = n2 + na * nc, n4 = n3 + na * nd, n5 = n4 + nb * nc,
             n6 = n5 + nb * nd;
@@ -367,26 +299,9 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
       dst = mv.K + (size_t)(fb + ib) * N + fd + id;
       s *= fac;
     }
-    if constexpr (F32)
-      atomicAdd(dst, f2d_any(s));
-    else
-      atomicAdd(dst, s);
+    atomicAdd(dst, s);
   }
   group_sync(gmask, G);
-}
-
-template <int G>
-__device__ void quartet(const KArgs &a, const ClassTables &ct, double *scr, int P, int Q, int gl,
-                        unsigned gmask) {
-  const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
-  // density-weighted Schwarz screening over the six shell blocks (Sec. 3.2)
-  const MolView mv = mol_view(a, ab.x);
-  const float b = quartet_bound(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
-  if (b < 0.0f) return;
-  if (b < a.fp32_cutoff_f)
-    quartet_body<G, float>(a, ct, scr, P, Q, gl, gmask, mv);
-  else
-    quartet_body<G, double>(a, ct, scr, P, Q, gl, gmask, mv);
 }
 
 template <int G>
@@ -420,7 +335,7 @@ __global__ void __launch_bounds__(128) k_jk(KArgs a) {
   auto drain = [&](int *q, int &n, const MolView &mv, int P, bool all) {
     const int k = all ? n : (n / NG) * NG;
     for (int i = 0; i < k; i += NG)
-      if (i + grp < k) quartet_body<G, double>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
+      if (i + grp < k) quartet_body<G>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
     __syncwarp();
     const int rest = n - k;  // < NG <= 32 entries move to the front
     const int v = lane < rest ? q[k + lane] : 0;
