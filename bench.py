@@ -196,6 +196,17 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(ms: float, dist, dev) -> float:
+    """The slowest rank's time (ms): every rank's replica must finish before
+    the whole job has processed world x its units."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def mixed_peak_frac(st, ms):
     """Roofline of the mixed path: the modelled FP64 and FP32 operations each
     over their own pipe's peak; `combined` = the fraction of the build time
@@ -385,10 +396,7 @@ def main():
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in evs]
     tot_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(tot_ms, dist, dev)
     ms = tot_ms / args.steps
     value = world * st["eris_schwarz"] * args.steps / (tot_ms * 1e-3)
 
@@ -409,10 +417,7 @@ def main():
     e_e.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = e_s.elapsed_time(e_e)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     e2e_value = world * st["eris_schwarz"] * args.steps / (e2e_ms * 1e-3)
     assert np.isfinite(Jh.numpy()).all() and np.isfinite(Kh.numpy()).all()
 
