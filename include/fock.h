@@ -215,8 +215,9 @@ FOCK_API fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_
                             double schwarz_thresh, double out[10]);
 
 /* Number of kernels one fock_build_jk call on this handle launches (density
- * preparation, one persistent ERI/digestion kernel per work tier, the final
- * symmetrisation); -1 for NULL.  Host only. */
+ * preparation, one persistent ERI/digestion kernel per work tier -- two for a
+ * group-kernel tier in mixed precision, its FP64 and its FP32 part -- and the
+ * final symmetrisation); -1 for NULL.  Host only. */
 FOCK_API int32_t fock_kernels_per_build(const fock_shellpairs *sp);
 
 /*

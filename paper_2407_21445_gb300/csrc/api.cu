@@ -281,7 +281,9 @@ int32_t fock_nbasis(const fock_shellpairs *sp) { return sp ? sp->nbf : -1; }
 int32_t fock_kernels_per_build(const fock_shellpairs *sp) {
   if (!sp) return -1;
   int n = 2;  // density preparation + symmetrisation
-  for (const Tier &t : sp->tiers) n += t.nunits > 0 ? 1 : 0;
+  const bool mixed = sp->opts.precision == FOCK_MIXED && sp->opts.fp32_cutoff > 0.0;
+  for (const Tier &t : sp->tiers)
+    if (t.nunits > 0) n += (mixed && t.reg_cb < 0) ? 2 : 1;  // group tiers: FP64 and FP32 parts
   return n;
 }
 
@@ -671,7 +673,7 @@ fock_status build_jk_events(const fock_shellpairs *sp, const double *D, double s
   const bool mixed = sp->opts.precision == FOCK_MIXED && sp->opts.fp32_cutoff > 0.0;
   const size_t dsh_bytes = sizeof(double) * (size_t)ns * ns;
   const size_t cnt_off = (dsh_bytes + 255) & ~(size_t)255;
-  const size_t df_off = (cnt_off + sizeof(int) * (nt + 1) + 255) & ~(size_t)255;
+  const size_t df_off = (cnt_off + sizeof(int) * (2 * nt + 1) + 255) & ~(size_t)255;
   const size_t dshf_off = mixed ? (df_off + sizeof(float) * (size_t)n * n + 255) & ~(size_t)255 : df_off;
   const size_t total = dshf_off + sizeof(float) * (size_t)ns * ns;
   char *scratch = nullptr;
@@ -683,7 +685,7 @@ fock_status build_jk_events(const fock_shellpairs *sp, const double *D, double s
   float *Dshf = (float *)(scratch + dshf_off);
   const bool chk = sync_check();
   const char *where = "memset";
-  e = cudaMemsetAsync(counters, 0, sizeof(int) * (nt + 1), stream);
+  e = cudaMemsetAsync(counters, 0, sizeof(int) * (2 * nt + 1), stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(J, 0, sizeof(double) * (size_t)n * n, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(K, 0, sizeof(double) * (size_t)n * n, stream);
   if (e == cudaSuccess) {
@@ -697,8 +699,8 @@ fock_status build_jk_events(const fock_shellpairs *sp, const double *D, double s
     where = tier_name;
     if (ev) e = cudaEventRecord(ev[t], stream);
     if (e == cudaSuccess)
-      e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, sp->prune_eps, J, K, counters + t, stream,
-                         Df, sp->opts.fp32_cutoff, Dshf);
+      e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, sp->prune_eps, J, K, counters + t,
+                         counters + nt + t, stream, Df, sp->opts.fp32_cutoff, Dshf);
     if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
   }
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[nt], stream);
@@ -747,7 +749,6 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
   const bool mixed = sp->opts.precision == FOCK_MIXED && sp->opts.fp32_cutoff > 0.0;
   for (size_t ui = 0; ui < sp->h_units.size(); ++ui) {
     const Unit &u = sp->h_units[ui];
-    const bool reg = sp->tiers[sp->h_unit_tier[ui]].reg_cb >= 0;  // only register kernels run FP32 quartets
     const int P = u.bra;
     const int2 ab = sp->h_ab[P];
     for (int Q = u.k0; Q < u.k1; ++Q) {
@@ -787,7 +788,7 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
       const double f = np * ft.prim[sp->h_cls[P]][sp->h_cls[Q]] + nbra * ft.bra[sp->h_cls[P]][sp->h_cls[Q]] +
                        12.0 * ne;
       fl += f;
-      if (mixed && reg && g * dm < sp->opts.fp32_cutoff) {
+      if (mixed && g * dm < sp->opts.fp32_cutoff) {
         q32 += 1;
         fl32 += f;
       }

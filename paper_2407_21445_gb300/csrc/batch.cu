@@ -211,7 +211,7 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
   const size_t o_dshf = off;
   off = al(off + sizeof(float) * bp->dsh_total);
   const size_t o_cnt = off;
-  off = al(off + sizeof(int) * (nt + 1));
+  off = al(off + sizeof(int) * (2 * nt + 1));
   const size_t o_df = off;
   if (bp->mixed) off = al(off + sizeof(float) * bp->n2_total);
   char *aux = nullptr;
@@ -255,7 +255,7 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
 cudaError_t enqueue(BatchPlan *bp, double tau, const cudaEvent_t *ev = nullptr) {
   cudaStream_t st = bp->st;
   cudaError_t e = cudaMemcpyAsync(bp->d_mt, bp->h_mt, sizeof(MolEntry) * bp->nmol, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(bp->counters, 0, sizeof(int) * (bp->tiers.size() + 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bp->counters, 0, sizeof(int) * (2 * bp->tiers.size() + 1), st);
   if (e == cudaSuccess) e = launch_zero_batch(bp->d_mt, bp->d_n2p, bp->nmol, bp->n2_total, st);
   if (e == cudaSuccess)
     e = launch_dprep_batch(bp->d_mt, bp->d_dshp, bp->nmol, bp->dsh_total, bp->dev.sbf, bp->dev.sl, bp->Dsh,
@@ -264,7 +264,8 @@ cudaError_t enqueue(BatchPlan *bp, double tau, const cudaEvent_t *ev = nullptr) 
     if (ev) e = cudaEventRecord(ev[t], st);
     if (e == cudaSuccess)
       e = launch_jk_tier_batch(bp->tiers[t], bp->dev, bp->d_mt, bp->Dsh, bp->Dshf, tau, bp->prim_eps,
-                               bp->counters + t, st, bp->mixed ? bp->cutoff : 0.0);
+                               bp->counters + t, bp->counters + bp->tiers.size() + t, st,
+                               bp->mixed ? bp->cutoff : 0.0);
   }
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[bp->tiers.size()], st);
   if (e == cudaSuccess) e = launch_symmetrize_batch(bp->d_mt, bp->d_n2p, bp->nmol, bp->n2_total, st);

@@ -190,9 +190,12 @@ cudaError_t launch_schwarz(const DevPairs &dp, double *Gpair, double *Gprim, cud
 cudaError_t launch_dprep(const double *D, int nbf, const int *sbf, const int *sl, int nshell,
                          double *Dsh, cudaStream_t st, float *Df = nullptr, float *Dshf = nullptr);
 // prim_eps: primitive-quartet screening factor (the handle's prune_eps; 0 = off)
+// counter2: work counter of the FP32 part of a group tier in mixed mode (may
+// be null when Df is null)
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh,
-                           double tau, double prim_eps, double *J, double *K, int *counter, cudaStream_t st,
-                           const float *Df = nullptr, double fp32_cutoff = 0.0, const float *Dshf = nullptr);
+                           double tau, double prim_eps, double *J, double *K, int *counter, int *counter2,
+                           cudaStream_t st, const float *Df = nullptr, double fp32_cutoff = 0.0,
+                           const float *Dshf = nullptr);
 cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st);
 // batched variants (one launch over every molecule of a batch)
 cudaError_t launch_zero_batch(const MolEntry *mt, const long long *n2_prefix, int nmol, long long total,
@@ -202,8 +205,8 @@ cudaError_t launch_dprep_batch(const MolEntry *mt, const long long *dsh_prefix, 
 cudaError_t launch_symmetrize_batch(const MolEntry *mt, const long long *n2_prefix, int nmol, long long total,
                                     cudaStream_t st);
 cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEntry *mt, const double *Dsh,
-                                 const float *Dshf, double tau, double prim_eps, int *counter, cudaStream_t st,
-                                 double fp32_cutoff);
+                                 const float *Dshf, double tau, double prim_eps, int *counter, int *counter2,
+                                 cudaStream_t st, double fp32_cutoff);
 cudaError_t configure_tier(Tier &t);
 int read_and_clear_status(cudaStream_t st, int *status);
 int read_bounds(long long out[2]);

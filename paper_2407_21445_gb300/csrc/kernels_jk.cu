@@ -69,10 +69,22 @@ __device__ __forceinline__ void group_sync(unsigned mask, int G) {
 // R^{(0)}_{tuv}, t+u+v <= L, into the returned buffer (one of R0/R1).
 // F must hold base values pref (-2alpha)^n F_n(T), n = 0..L; R0[0] = F[L].
 __constant__ double c_small[16] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15};
+__constant__ float c_smallf[16] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15};
 
 // x with its sign flipped when s == 1 (integer units only)
 __device__ __forceinline__ double neg_if(double x, int s) {
   return __longlong_as_double(__double_as_longlong(x) ^ ((long long)s << 63));
+}
+__device__ __forceinline__ float neg_if(float x, int s) {
+  return __int_as_float(__float_as_int(x) ^ (s << 31));
+}
+
+template <class Real>
+__device__ __forceinline__ Real small_int(int i) {
+  if constexpr (sizeof(Real) == 8)
+    return c_small[i];
+  else
+    return c_smallf[i];
 }
 
 template <int G, class Real>
@@ -89,13 +101,13 @@ __device__ __forceinline__ Real *hermite_r(const ClassTables &ct, int L, Real X,
         int t = ct.hvec[e][0], u = ct.hvec[e][1], w = ct.hvec[e][2];
         if (t > 0) {
           v = X * cur[hidx(t - 1, u, w)];
-          if (t > 1) v = fma(c_small[t - 1], cur[hidx(t - 2, u, w)], v);
+          if (t > 1) v = fma(small_int<Real>(t - 1), cur[hidx(t - 2, u, w)], v);
         } else if (u > 0) {
           v = Y * cur[hidx(t, u - 1, w)];
-          if (u > 1) v = fma(c_small[u - 1], cur[hidx(t, u - 2, w)], v);
+          if (u > 1) v = fma(small_int<Real>(u - 1), cur[hidx(t, u - 2, w)], v);
         } else {
           v = Z * cur[hidx(t, u, w - 1)];
-          if (w > 1) v = fma(c_small[w - 1], cur[hidx(t, u, w - 2)], v);
+          if (w > 1) v = fma(small_int<Real>(w - 1), cur[hidx(t, u, w - 2)], v);
         }
       }
       nxt[e] = v;
@@ -108,11 +120,43 @@ __device__ __forceinline__ Real *hermite_r(const ClassTables &ct, int L, Real X,
   return cur;
 }
 
-// One contracted quartet on a group of G lanes (FP64).
+// FP32 seeds for the group kernel (lanes over m), R0[0] = F[L].
 template <int G>
+__device__ __forceinline__ void boys_seeds_rt_f32(const float *__restrict__ tab, float T, float pref, float m2a, int L,
+                                                  float *F, float *R0, int gl) {
+  for (int m = gl; m <= L; m += G) {
+    float f;
+    if (T < (float)BOYS_TMAX) {
+      const int gi = __float2int_rn(T * (float)BOYS_INVH);
+      const float x = (float)gi * (float)BOYS_H - T;
+      const float4 *c = reinterpret_cast<const float4 *>(tab + ((size_t)gi * (LTOT + 1) + m) * BOYS_TAYLOR);
+      const float4 c03 = __ldg(c);
+      const float2 c45 = __ldg(reinterpret_cast<const float2 *>(c + 1));
+      f = fmaf(c45.y, x, c45.x);
+      f = fmaf(f, x, c03.w);
+      f = fmaf(f, x, c03.z);
+      f = fmaf(f, x, c03.y);
+      f = fmaf(f, x, c03.x);
+    } else {
+      const float rt = rsqrtf(T), it = rt * rt;
+      f = 0.886226925452758f * rt;
+      for (int k = 1; k <= m; ++k) f *= ((float)k - 0.5f) * it;
+    }
+    float c = pref;
+    for (int k = 0; k < m; ++k) c *= m2a;
+    F[m] = f * c;
+    if (m == L) R0[0] = F[m];
+  }
+}
+
+// One contracted quartet on a group of G lanes, in FP64 (Real = double) or
+// in FP32 (Real = float, the mixed-precision path below the cutoff: FP32
+// table, pair-relative centres, FP32 copies of U, E and D, exact FP32->FP64
+// conversion of every digested element before the FP64 atomic add).
+template <int G, class Real>
 __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_d, int P, int Q, int gl,
                              unsigned gmask, const MolView &mv) {
-  using Real = double;
+  constexpr bool F32 = sizeof(Real) == 4;
   const DevPairs &dp = a.dp;
   const int2 ab = dp.ab[P], cd = dp.ab[Q];
   const int sA = ab.x, sB = ab.y, sC = cd.x, sD = cd.y;
@@ -137,7 +181,18 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
   Real *R0 = Yh + nhab * ncd;
   Real *R1 = R0 + nhL;
   Real *F = R1 + nhL;
-  const Real *Epool = dp.E;
+  const Real *Epool;
+  if constexpr (F32)
+    Epool = dp.Ef;
+  else
+    Epool = dp.E;
+  float ACx = 0.f, ACy = 0.f, ACz = 0.f;
+  if constexpr (F32) {
+    const float *ha = dp.shl + 6 * sA, *hc = dp.shl + 6 * sC;
+    ACx = (ha[0] - hc[0]) + (ha[3] - hc[3]);
+    ACy = (ha[1] - hc[1]) + (ha[4] - hc[4]);
+    ACz = (ha[2] - hc[2]) + (ha[5] - hc[5]);
+  }
 
   for (int i = gl; i < nab * ncd; i += G) eri[i] = Real(0);
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
@@ -151,10 +206,24 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
       if (prim_skip(a, mv, ps, ip, jq)) break;
       const Real *EQ = Epool + dp.eoff[jq];
-      const PrimQuartet q = prim_quartet(dp.pz[ip], dp.pf[ip], dp.U[ip], dp.pz[jq], dp.pf[jq], dp.U[jq]);
-      FK_CHECK(q.T >= 0.0 && q.T == q.T && q.gi <= BOYS_NGRID - 1, 9, jq);
-      const Real X = q.X, Y = q.Y, Z = q.Z;
-      boys_seeds_rt<G>(a.boys, q, L, F, R0, gl);
+      Real X, Y, Z;
+      if constexpr (F32) {
+        const float4 PA = dp.paf[ip], QC = dp.paf[jq];
+        X = PA.x - QC.x + ACx;
+        Y = PA.y - QC.y + ACy;
+        Z = PA.z - QC.z + ACz;
+        const float rs = rsqrtf(PA.w + QC.w);
+        const float alpha = (PA.w * QC.w) * (rs * rs);
+        const float T = alpha * fmaf(X, X, fmaf(Y, Y, Z * Z));
+        boys_seeds_rt_f32<G>(a.boysf, T, dp.Uf[ip] * dp.Uf[jq] * rs, -2.0f * alpha, L, F, R0, gl);
+      } else {
+        const PrimQuartet q = prim_quartet(dp.pz[ip], dp.pf[ip], dp.U[ip], dp.pz[jq], dp.pf[jq], dp.U[jq]);
+        FK_CHECK(q.T >= 0.0 && q.T == q.T && q.gi <= BOYS_NGRID - 1, 9, jq);
+        X = q.X;
+        Y = q.Y;
+        Z = q.Z;
+        boys_seeds_rt<G>(a.boys, q, L, F, R0, gl);
+      }
       group_sync(gmask, G);
       const Real *R = hermite_r<G, Real>(ct, L, X, Y, Z, F, R0, R1, gl, gmask);
       // ket transform, accumulated over ket primitives
@@ -220,7 +289,11 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
   if (P == Q) fac *= Real(0.5);
   const int N = mv.N;
   const int fa = dp.sbf[sA], fb = dp.sbf[sB], fc = dp.sbf[sC], fd = dp.sbf[sD];
-  const Real *Dm = mv.D;
+  const Real *Dm;
+  if constexpr (F32)
+    Dm = mv.Df;
+  else
+    Dm = mv.D;
   const Real fac2 = Real(2) * fac;
   const int n1 = nab, n2 = n1 + ncd, n3 = n2 + na * nc, n4 = n3 + na * nd, n5 = n4 + nb * nc,
             n6 = n5 + nb * nd;
@@ -299,12 +372,19 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
       dst = mv.K + (size_t)(fb + ib) * N + fd + id;
       s *= fac;
     }
-    atomicAdd(dst, s);
+    if constexpr (F32)
+      atomicAdd(dst, f2d_any(s));
+    else
+      atomicAdd(dst, s);
   }
   group_sync(gmask, G);
 }
 
-template <int G>
+// MODE 0: every surviving quartet in FP64 (FP64 build).  Mixed build, one
+// launch per part: MODE 1 takes the survivors whose bound is at least the FP32
+// cutoff (FP64 body), MODE 2 those below it (FP32 body).  Each launch holds a
+// single body, so a warp never alternates between the two.
+template <int G, int MODE>
 __global__ void __launch_bounds__(128) k_jk(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   {
@@ -321,21 +401,21 @@ __global__ void __launch_bounds__(128) k_jk(KArgs a) {
   double *scr = scr_base + (size_t)(warp * NG + grp) * a.stride;
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
   // Warp-level work queue, as in the register kernels: the unit's kets are
-  // screened 32 at a time and the survivors appended to a queue that is
-  // drained NG quartets at a time (one per group), so no group holds a
-  // screened quartet while the others compute.  The group kernels evaluate
-  // every quartet in FP64, also in mixed mode: they are bound by instruction
-  // issue and lane utilisation rather than by the FP64 pipe (ncu: FP64 pipe
-  // ~50 % active, ~17 of 32 lanes active per instruction), an FP32 body runs
-  // about as many instructions, and switching between the two bodies in one
-  // kernel stalled on instruction fetch.
+  // screened 32 at a time and the survivors of this launch's part appended to
+  // a queue that is drained NG quartets at a time (one per group), so no
+  // group holds a screened quartet while the others compute.
   __shared__ int queues[4][64];
   int *q64 = queues[warp];
   const unsigned lt = (1u << lane) - 1u;
   auto drain = [&](int *q, int &n, const MolView &mv, int P, bool all) {
     const int k = all ? n : (n / NG) * NG;
     for (int i = 0; i < k; i += NG)
-      if (i + grp < k) quartet_body<G>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
+      if (i + grp < k) {
+        if constexpr (MODE == 2)
+          quartet_body<G, float>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
+        else
+          quartet_body<G, double>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
+      }
     __syncwarp();
     const int rest = n - k;  // < NG <= 32 entries move to the front
     const int v = lane < rest ? q[k + lane] : 0;
@@ -359,7 +439,9 @@ __global__ void __launch_bounds__(128) k_jk(KArgs a) {
         const int2 cd = a.dp.ab[Q];
         b = quartet_bound(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
       }
-      const bool keep = b >= 0.0f;
+      bool keep = b >= 0.0f;
+      if constexpr (MODE == 1) keep = keep && !(b < a.fp32_cutoff_f);
+      if constexpr (MODE == 2) keep = keep && b < a.fp32_cutoff_f;
       const unsigned m64 = __ballot_sync(0xffffffffu, keep);
       if (keep) q64[n64 + __popc(m64 & lt)] = Q;
       n64 += __popc(m64);
@@ -658,6 +740,43 @@ cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st) {
 }
 
 template <int G>
+static cudaError_t set_smem_g(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_jk<G, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_jk<G, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_jk<G, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
+
+// One group tier: a single FP64 launch, or in mixed mode (a.fp32_cutoff > 0)
+// the FP64 part and then the FP32 part, each drawing units from its own counter.
+template <int G>
+static cudaError_t launch_g(const Tier &t, KArgs a, int threads, cudaStream_t st, int *counter2) {
+  if (a.fp32_cutoff > 0.0) {
+    if (!counter2) return cudaErrorInvalidValue;
+    k_jk<G, 1><<<t.blocks, threads, t.smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    a.counter = counter2;
+    k_jk<G, 2><<<t.blocks, threads, t.smem, st>>>(a);
+  } else {
+    k_jk<G, 0><<<t.blocks, threads, t.smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_group(const Tier &t, const KArgs &a, int threads, cudaStream_t st, int *counter2) {
+  switch (t.G) {
+    case 1: return launch_g<1>(t, a, threads, st, counter2);
+    case 2: return launch_g<2>(t, a, threads, st, counter2);
+    case 4: return launch_g<4>(t, a, threads, st, counter2);
+    case 8: return launch_g<8>(t, a, threads, st, counter2);
+    case 16: return launch_g<16>(t, a, threads, st, counter2);
+    case 32: return launch_g<32>(t, a, threads, st, counter2);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int G>
 static cudaError_t configure_g(Tier &t) {
   const size_t per_warp = (size_t)(32 / G) * t.stride * sizeof(double);
   // 227 KB per block, less the kernel's static work queues
@@ -667,10 +786,10 @@ static cudaError_t configure_g(Tier &t) {
   if (TAB_BYTES + wpb * per_warp > limit) return cudaErrorInvalidValue;
   t.warps_per_block = wpb;
   t.smem = TAB_BYTES + wpb * per_warp;
-  cudaError_t e = cudaFuncSetAttribute(k_jk<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+  cudaError_t e = set_smem_g<G>(t.smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jk<G>, 32 * wpb, t.smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jk<G, 0>, 32 * wpb, t.smem);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -716,12 +835,12 @@ cudaError_t configure_tier(Tier &t) {
 // every handle; raise it to this tier's need before launching.
 static cudaError_t set_group_smem(const Tier &t) {
   switch (t.G) {
-    case 1: return cudaFuncSetAttribute(k_jk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
-    case 2: return cudaFuncSetAttribute(k_jk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
-    case 4: return cudaFuncSetAttribute(k_jk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
-    case 8: return cudaFuncSetAttribute(k_jk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
-    case 16: return cudaFuncSetAttribute(k_jk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
-    case 32: return cudaFuncSetAttribute(k_jk<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+    case 1: return set_smem_g<1>(t.smem);
+    case 2: return set_smem_g<2>(t.smem);
+    case 4: return set_smem_g<4>(t.smem);
+    case 8: return set_smem_g<8>(t.smem);
+    case 16: return set_smem_g<16>(t.smem);
+    case 32: return set_smem_g<32>(t.smem);
   }
   return cudaErrorInvalidValue;
 }
@@ -735,8 +854,8 @@ static void set_screen_args(KArgs &a, double tau, const float *Dshf, double prim
 }
 
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh, double tau,
-                           double prim_eps, double *J, double *K, int *counter, cudaStream_t st, const float *Df,
-                           double fp32_cutoff, const float *Dshf) {
+                           double prim_eps, double *J, double *K, int *counter, int *counter2, cudaStream_t st,
+                           const float *Df, double fp32_cutoff, const float *Dshf) {
   if (t.nunits == 0) return cudaSuccess;
   if (t.reg_cb >= 0) {
     KArgs a;
@@ -784,28 +903,18 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
   a.boys = dev_boys();
   a.tabs = dev_class_tables();
   a.mt = nullptr;
-  a.fp32_cutoff = 0.0;  // the group kernels evaluate every quartet in FP64
-  a.fp32_cutoff_f = 0.0f;
-  a.Df = nullptr;
+  a.fp32_cutoff = Df ? fp32_cutoff : 0.0;
+  a.fp32_cutoff_f = (float)a.fp32_cutoff;
+  a.Df = Df;
   a.boysf = dev_boys_f();
   set_screen_args(a, tau, Dshf, prim_eps);
-  const dim3 blk(32 * t.warps_per_block);
-  switch (t.G) {
-    case 1: k_jk<1><<<t.blocks, blk, t.smem, st>>>(a); break;
-    case 2: k_jk<2><<<t.blocks, blk, t.smem, st>>>(a); break;
-    case 4: k_jk<4><<<t.blocks, blk, t.smem, st>>>(a); break;
-    case 8: k_jk<8><<<t.blocks, blk, t.smem, st>>>(a); break;
-    case 16: k_jk<16><<<t.blocks, blk, t.smem, st>>>(a); break;
-    case 32: k_jk<32><<<t.blocks, blk, t.smem, st>>>(a); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return launch_group(t, a, 32 * t.warps_per_block, st, counter2);
 }
 
 // One tier of a batched build: same kernels, per-molecule D/J/K from mt.
 cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEntry *mt, const double *Dsh,
-                                 const float *Dshf, double tau, double prim_eps, int *counter, cudaStream_t st,
-                                 double fp32_cutoff) {
+                                 const float *Dshf, double tau, double prim_eps, int *counter, int *counter2,
+                                 cudaStream_t st, double fp32_cutoff) {
   if (t.nunits == 0) return cudaSuccess;
   KArgs a;
   memset(&a, 0, sizeof(a));
@@ -822,7 +931,7 @@ cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEnt
   a.tabs = dev_class_tables();
   a.boysf = dev_boys_f();
   a.mt = mt;
-  a.fp32_cutoff = t.reg_cb >= 0 ? fp32_cutoff : 0.0;  // group kernels: FP64 only
+  a.fp32_cutoff = fp32_cutoff;
   a.fp32_cutoff_f = (float)a.fp32_cutoff;
   set_screen_args(a, tau, Dshf, prim_eps);
   const int threads = 32 * t.warps_per_block;
@@ -835,16 +944,7 @@ cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEnt
   }
   cudaError_t ae = set_group_smem(t);
   if (ae != cudaSuccess) return ae;
-  switch (t.G) {
-    case 1: k_jk<1><<<t.blocks, threads, t.smem, st>>>(a); break;
-    case 2: k_jk<2><<<t.blocks, threads, t.smem, st>>>(a); break;
-    case 4: k_jk<4><<<t.blocks, threads, t.smem, st>>>(a); break;
-    case 8: k_jk<8><<<t.blocks, threads, t.smem, st>>>(a); break;
-    case 16: k_jk<16><<<t.blocks, threads, t.smem, st>>>(a); break;
-    case 32: k_jk<32><<<t.blocks, threads, t.smem, st>>>(a); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return launch_group(t, a, threads, st, counter2);
 }
 
 int read_bounds(long long out[2]) {

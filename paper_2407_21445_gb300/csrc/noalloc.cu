@@ -74,7 +74,8 @@ extern "C" fock_status fock_build_jk_noalloc(const fock_shellpairs *sp, const do
   if (e == cudaSuccess) e = cudaMemsetAsync(K, 0, sizeof(double) * (size_t)n * n, stream);
   if (e == cudaSuccess) e = launch_dprep(D, n, sp->dev.sbf, sp->dev.sl, ns, Dsh, stream);
   for (size_t t = 0; t < nt && e == cudaSuccess; ++t)
-    e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, sp->prune_eps, J, K, counters + t, stream);
+    e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, sp->prune_eps, J, K, counters + t, nullptr,
+                       stream);
   if (e == cudaSuccess) e = launch_symmetrize(J, K, n, stream);
   if (e == cudaSuccess) return FOCK_OK;
   return e == cudaErrorMemoryAllocation ? FOCK_ERR_OOM : FOCK_ERR_CUDA;

@@ -96,8 +96,7 @@ def test_mixed_water64_blocks(env):
 @pytest.mark.parametrize("group", [0, 1, 4, 32])
 def test_mixed_group_kernels(env, group):
     """Every class pair on the group-cooperative kernels (no register
-    kernels), for several group sizes: in mixed mode they evaluate every
-    quartet in FP64, so the result meets the FP64 tolerance."""
+    kernels), for several group sizes: their FP64 and FP32 parts."""
     rng = np.random.Generator(np.random.PCG64(301 + group))
     bas = molgen.random_shells(rng, [0, 1, 2, 3, 0, 1, 2, 0], spread=6.0, kmax=3)
     n = oracle.nbf(bas)
@@ -106,5 +105,4 @@ def test_mixed_group_kernels(env, group):
     J, K, st = mixed_jk(env, bas, D, 1e-11, cutoff=1e-4, reg_max_L=-1, group_override=group)
     Jo, Ko = oracle.jk(bas, D, 1e-11)
     check(J, K, Jo, Ko, D)
-    assert st["quartets_fp32"] == 0
-    assert np.abs(J - Jo).max() <= 1e-10 and np.abs(K - Ko).max() <= 1e-10
+    assert st["quartets_fp32"] > 0
