@@ -80,8 +80,12 @@ typedef struct {
   int32_t precision;    /* FOCK_FP64 (default) or FOCK_MIXED                     */
   double fp32_cutoff;   /* mixed path: quartets with G_ab G_cd Dmax below this
                            bound are evaluated in FP32 (default 1e-5)           */
-  double prune_eps;     /* primitive pair [ab] dropped when G_[ab] Gmax <
-                           tau * prune_eps (default 1e-3; 0 disables)           */
+  double prune_eps;     /* primitive screening (Sec. 3.2, 3.3): primitive pair
+                           [ab] dropped when G_[ab] Gmax < tau * prune_eps, and
+                           inside a quartet that passes, primitive quartet
+                           [ab|cd] skipped when G_[ab] G_[cd] Dmax < tau *
+                           prune_eps (Dmax the six-block density maximum)
+                           (default 1e-3; 0 disables both)                       */
   int32_t group_override; /* 0 = autotuned per class pair; 1..32 = lanes per
                              quartet forced for every class pair (testing)     */
   int32_t warp_scratch;   /* shared-memory doubles one warp may use for the
