@@ -227,15 +227,19 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
       group_sync(gmask, G);
       const Real *R = hermite_r<G, Real>(ct, L, X, Y, Z, F, R0, R1, gl, gmask);
       // ket transform, accumulated over ket primitives
+      // elements in ket-component-major order: the lanes of a group then work
+      // on the same ket component (same Hermite box, same trip counts) for
+      // consecutive bra Hermite indices
       for (int it = gl; it < nhab * ncd; it += G) {
-        const int ph = it / ncd, kc = it - ph * ncd;
+        const int kc = it / nhab, ph = it - kc * nhab;
         const int tp = ct.hvec[ph][0], up = ct.hvec[ph][1], vp = ct.hvec[ph][2];
         const int ic = kc / nd, id = kc - ic * nd;
         const uint8_t *cc = ct.comp[lc][ic], *dd = ct.comp[ld][id];
         const int Tx = cc[0] + dd[0], Ty = cc[1] + dd[1], Tz = cc[2] + dd[2];
         const Real *Eq = EQ + ct.eoff[ck][kc];
         // two independent accumulation chains (even / odd v) for latency
-        Real acc0 = Yh[it], acc1 = Real(0);
+        const int yi = ph * ncd + kc;  // Yh layout: [bra Hermite index][ket component]
+        Real acc0 = Yh[yi], acc1 = Real(0);
         int e = 0;
         for (int t = 0; t <= Tx; ++t)
           for (int u = 0; u <= Ty; ++u) {
@@ -251,7 +255,7 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
               ++e;
             }
           }
-        Yh[it] = acc0 + acc1;
+        Yh[yi] = acc0 + acc1;
       }
       group_sync(gmask, G);
     }

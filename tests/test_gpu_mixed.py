@@ -106,3 +106,21 @@ def test_mixed_group_kernels(env, group):
     Jo, Ko = oracle.jk(bas, D, 1e-11)
     check(J, K, Jo, Ko, D)
     assert st["quartets_fp32"] > 0
+
+
+def test_mixed_kernel_count(env):
+    """A mixed build launches one extra kernel per group-kernel tier (its
+    FP32 part); with every class pair on register kernels the counts agree."""
+    torch, fk = env
+    p = molgen.problem(0)
+    n64 = fk.JKBuilder(p.basis, p.tau, fk.make_opts(precision=fk.FOCK_FP64))
+    nmx = fk.JKBuilder(p.basis, p.tau, fk.make_opts(precision=fk.FOCK_MIXED))
+    k64, kmx = fk.fock_kernels_per_build(n64.handle), fk.fock_kernels_per_build(nmx.handle)
+    assert kmx > k64  # the trimer has d shells, so group tiers exist
+    b = molgen.single_shell_basis([(1, np.zeros(3), np.array([1.0]), np.array([1.0])),
+                                   (0, np.array([0.0, 0.0, 1.5]), np.array([0.8]), np.array([1.0]))])
+    r64 = fk.JKBuilder(b, 1e-12, fk.make_opts(precision=fk.FOCK_FP64))
+    rmx = fk.JKBuilder(b, 1e-12, fk.make_opts(precision=fk.FOCK_MIXED))
+    assert fk.fock_kernels_per_build(r64.handle) == fk.fock_kernels_per_build(rmx.handle)
+    for x in (n64, nmx, r64, rmx):
+        x.close()
