@@ -103,7 +103,12 @@ const FlopTable &flop_table() {
   return t;
 }
 
+// Contraction bins: pairs with the same number of kept primitive pairs share
+// a bin up to 16, then bins 4 wide, so that the 32 kets a warp takes have
+// nearly equal primitive loops (lanes of a warp wait for the longest).
+constexpr bool kFineBins = true;
 int bucket_of(int nprim) {
+  if (kFineBins) return nprim <= 16 ? nprim : 16 + (nprim - 13) / 4;
   int b = 0;
   while ((1 << b) < nprim) ++b;
   return b;  // 1 -> 0, 2 -> 1, 3..4 -> 2, 5..8 -> 3, ...
@@ -485,13 +490,14 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
 
   // ---- bins and work units --------------------------------------------------
   struct Bin {
-    int begin, end, cls, bucket;
+    int begin, end, cls, bucket, nprim;  // nprim: largest kept primitive-pair count
   };
   std::vector<Bin> bins;
   for (int i = 0; i < npair; ++i) {
     if (bins.empty() || bins.back().cls != keep[i].cls || bins.back().bucket != keep[i].bucket)
-      bins.push_back({i, i, keep[i].cls, keep[i].bucket});
+      bins.push_back({i, i, keep[i].cls, keep[i].bucket, 0});
     bins.back().end = i + 1;
+    bins.back().nprim = std::max(bins.back().nprim, keep[i].nkeep);
   }
   struct Task {
     int bra, ket;  // bin indices
@@ -508,7 +514,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
       int lxa, lxb, lya, lyb;
       class_l(X.cls, lxa, lxb);
       class_l(Y.cls, lya, lyb);
-      const double px = 1 << X.bucket, py = 1 << Y.bucket;
+      const double px = X.nprim, py = Y.nprim;
       const int Lx = lxa + lxb, Ly = lya + lyb, nx = ncart(lxa) * ncart(lxb), ny = ncart(lya) * ncart(lyb);
       // cost with X as bra vs Y as bra
       const double cxy = px * (py * flops_prim(Lx, Lx + Ly, Y.cls) + flops_bra(X.cls, ny));
