@@ -366,17 +366,20 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
 // One quartet: screening, then the FP32 path below the mixed-precision
 // cutoff (0 in the FP64 mode) or the FP64 path.
 
-// Warp-level work queue: the unit's kets are screened 32 at a time and the
-// surviving ones appended to an FP64 or an FP32 queue (ballot + prefix
-// popcount); each full queue is drained 32 quartets at a time, so every batch
-// runs one precision with all lanes busy and screened-out quartets cost no
-// lane time.
+// Warp-level work queue: a unit's kets are screened 32 at a time and the
+// surviving (bra, ket) pairs appended to an FP64 or an FP32 queue (ballot +
+// prefix popcount); each full queue is drained 32 quartets at a time, so every
+// batch runs one precision with all lanes busy and screened-out quartets cost
+// no lane time.  The queues carry over from one unit to the next (all units
+// of a launch are of one class pair), so a warp leaves a partly filled batch
+// only once, after its last unit.
 template <int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void drain_reg(const KArgs &a, const MolView &mv, int P, int *q, int n, bool fp32,
+__device__ __forceinline__ void drain_reg(const KArgs &a, const int *qp, const int *qq, int n, bool fp32,
                                           double *eri_col, int lane) {
   if (lane < n) {
-    const int Q = q[lane];
+    const int P = qp[lane], Q = qq[lane];
     const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
+    const MolView mv = mol_view(a, ab.x);
     if (fp32)
       quartet_reg_f32<LA, LB, LC, LD>(a, mv, P, Q, ab.x, ab.y, cd.x, cd.y);
     else
@@ -387,11 +390,27 @@ __device__ __forceinline__ void drain_reg(const KArgs &a, const MolView &mv, int
 template <int LA, int LB, int LC, int LD>
 __global__ void __launch_bounds__(128) k_reg(KArgs a) {
   extern __shared__ __align__(16) double reg_smem[];
-  __shared__ int queues[4][2][64];  // per warp: FP64 and FP32 ket queues
+  __shared__ int queues[4][2][2][64];  // per warp: FP64 / FP32 queue of (bra, ket)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double *eri_col = reg_smem + threadIdx.x;
-  int *q64 = queues[warp][0], *q32 = queues[warp][1];
+  int *p64 = queues[warp][0][0], *q64 = queues[warp][0][1];
+  int *p32 = queues[warp][1][0], *q32 = queues[warp][1][1];
   const unsigned lt = (1u << lane) - 1u;
+  // drain the first 32 entries of a queue and move the rest (< 32) forward
+  auto drain32 = [&](int *qp, int *qq, int &n, bool fp32) {
+    drain_reg<LA, LB, LC, LD>(a, qp, qq, 32, fp32, eri_col, lane);
+    __syncwarp();
+    const bool mv_ = lane + 32 < n;
+    const int rp = mv_ ? qp[lane + 32] : 0, rq = mv_ ? qq[lane + 32] : 0;
+    __syncwarp();
+    if (mv_) {
+      qp[lane] = rp;
+      qq[lane] = rq;
+    }
+    n -= 32;
+    __syncwarp();
+  };
+  int n64 = 0, n32 = 0;
   for (;;) {
     const int u = next_unit(a.counter, lane);
     if (u >= a.nunits) break;
@@ -399,7 +418,6 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
     const int P = un.bra;
     const int2 ab = a.dp.ab[P];
     const MolView mv = mol_view(a, ab.x);
-    int n64 = 0, n32 = 0;
     for (int c = un.k0; c < un.k1; c += 32) {
       const int Q = c + lane;
       float b = -1.0f;
@@ -409,34 +427,25 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
       }
       const bool is32 = b >= 0.0f && b < a.fp32_cutoff_f, is64 = b >= 0.0f && !is32;
       const unsigned m64 = __ballot_sync(0xffffffffu, is64), m32 = __ballot_sync(0xffffffffu, is32);
-      if (is64) q64[n64 + __popc(m64 & lt)] = Q;
-      if (is32) q32[n32 + __popc(m32 & lt)] = Q;
+      if (is64) {
+        const int k = n64 + __popc(m64 & lt);
+        p64[k] = P;
+        q64[k] = Q;
+      }
+      if (is32) {
+        const int k = n32 + __popc(m32 & lt);
+        p32[k] = P;
+        q32[k] = Q;
+      }
       n64 += __popc(m64);
       n32 += __popc(m32);
       __syncwarp();
-      if (n64 >= 32) {
-        drain_reg<LA, LB, LC, LD>(a, mv, P, q64, 32, false, eri_col, lane);
-        __syncwarp();
-        const int rest = lane + 32 < n64 ? q64[lane + 32] : 0;
-        __syncwarp();
-        if (lane + 32 < n64) q64[lane] = rest;
-        n64 -= 32;
-        __syncwarp();
-      }
-      if (n32 >= 32) {
-        drain_reg<LA, LB, LC, LD>(a, mv, P, q32, 32, true, eri_col, lane);
-        __syncwarp();
-        const int rest = lane + 32 < n32 ? q32[lane + 32] : 0;
-        __syncwarp();
-        if (lane + 32 < n32) q32[lane] = rest;
-        n32 -= 32;
-        __syncwarp();
-      }
+      if (n64 >= 32) drain32(p64, q64, n64, false);
+      if (n32 >= 32) drain32(p32, q32, n32, true);
     }
-    drain_reg<LA, LB, LC, LD>(a, mv, P, q64, n64, false, eri_col, lane);
-    drain_reg<LA, LB, LC, LD>(a, mv, P, q32, n32, true, eri_col, lane);
-    __syncwarp();
   }
+  drain_reg<LA, LB, LC, LD>(a, p64, q64, n64, false, eri_col, lane);
+  drain_reg<LA, LB, LC, LD>(a, p32, q32, n32, true, eri_col, lane);
 }
 
 // (bra class, ket class) pairs served by register kernels: total L <= 4
