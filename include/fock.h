@@ -151,7 +151,11 @@ FOCK_API int32_t fock_nbasis(const fock_shellpairs *sp);
  * direct method (Sec. 2.2): every symmetry-unique contracted shell quartet
  * (Sec. 2.3, 8-fold symmetry) whose density-weighted Schwarz bound
  * G_ab G_cd max(|D_ab|,|D_ac|,|D_ad|,|D_bc|,|D_bd|,|D_cd|) is not below
- * schwarz_thresh (Sec. 3.2) is evaluated and digested into J and K.
+ * schwarz_thresh (Sec. 3.2) is evaluated and digested into J and K.  Inside
+ * such a quartet, a primitive quartet [ab|cd] is skipped when
+ * G_[ab] G_[cd] Dmax < schwarz_thresh * prune_eps (Sec. 3.2, 3.3).  With
+ * precision FOCK_MIXED, a quartet whose bound is below fp32_cutoff is
+ * evaluated in FP32 and its contributions are accumulated in FP64.
  *   D: device, N x N row-major float64, symmetric (read).
  *   J, K: device, N x N row-major float64 (overwritten).
  *   schwarz_thresh >= the value the handle was built with.
@@ -191,7 +195,15 @@ FOCK_API fock_status fock_build_jk_noalloc(const fock_shellpairs *sp, const doub
 /*
  * J and K for nmol independent molecules in one pass: bases[i], D[i], J[i],
  * K[i] as in fock_build_jk (all device pointers; the pointer arrays themselves
- * are host memory read during the call).
+ * are host memory read during the call).  All handles must have been built
+ * with the same options and threshold.  The molecules' work lists are merged
+ * per kernel tier (one launch per tier covers every molecule); the merged
+ * plan is cached per list of handles (the four most recent lists) and its
+ * launches are captured once into a CUDA graph on a library-owned stream,
+ * which is ordered after `stream` and `stream` after it by events.  The
+ * result is the same as nmol calls of fock_build_jk.
+ * Errors: FOCK_ERR_INVALID_ARG (null pointers, nmol < 0, handles with
+ * different options), FOCK_ERR_OOM, FOCK_ERR_CUDA; nmol == 0 does nothing.
  */
 FOCK_API fock_status fock_build_jk_batched(const fock_shellpairs *const *bases, int32_t nmol,
                                   const double *const *D, double schwarz_thresh,
