@@ -397,8 +397,12 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
                           sqrt(2.0 / sqrt(kPi)));
           all.eoff.push_back((int)all.E.size());
           const size_t e0 = all.E.size();
-          all.E.resize(e0 + ct.nE[pair_class(la, lb)]);
+          const int ne = ct.nE[pair_class(la, lb)];
+          all.E.resize(e0 + ne);
           hermite_pair(la, lb, al, A, be, B, true, all.E.data() + e0);
+          // the pair factor Us_P is folded into the pair's Hermite coefficients, so
+          // that a primitive quartet's seed prefactor is 1/sqrt(zeta + eta) alone
+          for (int k = 0; k < ne; ++k) all.E[e0 + k] *= all.U.back();
         }
       all.ab.push_back(make_int2(a, b));
       all.prim.push_back(make_int2(first, Ka * Kb));

@@ -38,20 +38,22 @@ struct PrimQuartet {
   double X, Y, Z;   // P - Q
   double T;         // alpha |P - Q|^2
   double m2a;       // -2 alpha
-  double pref;      // U_P U_Q 2 sqrt(alpha/pi)
+  double pref;      // 1/sqrt(zeta + eta); the pair factors U_P sqrt(zeta) (2/sqrt(pi))^(1/2)
+                    // are folded into the Hermite coefficients, so pref times them is
+                    // U_P U_Q 2 sqrt(alpha/pi)
   int gi;           // Boys grid index (T < BOYS_TMAX) or -1 (asymptotic)
   double Ti;        // grid abscissa i*h (exact)
   float Tf;         // T on the FP32 units (seed of the asymptotic rsqrt)
 };
 
-// P4 = (Px, Py, Pz, zeta), Pf = the same in FP32, Us = U_P sqrt(zeta) (2/sqrt(pi))^(1/2).
-__device__ __forceinline__ PrimQuartet prim_quartet(const PZ &P4, const float4 &Pf, double UsP, const PZ &Q4,
-                                                    const float4 &Qf, double UsQ) {
+// P4 = (Px, Py, Pz, zeta), Pf = the same in FP32.
+__device__ __forceinline__ PrimQuartet prim_quartet(const PZ &P4, const float4 &Pf, const PZ &Q4,
+                                                    const float4 &Qf) {
   PrimQuartet r;
   const double s = P4.w + Q4.w;
   const float sf = Pf.w + Qf.w;
   const double rs = rsqrt_nh(s, sf);
-  r.pref = UsP * UsQ * rs;
+  r.pref = rs;
   const double alpha = (P4.w * Q4.w) * (rs * rs);
   r.m2a = -2.0 * alpha;
   r.X = P4.x - Q4.x;

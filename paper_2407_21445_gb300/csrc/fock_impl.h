@@ -79,9 +79,9 @@ struct DevPairs {
   // primitive pairs
   const PZ *pz;        // (Px, Py, Pz, zeta)
   const float4 *pf;    // the same in FP32 (grid indices, seeds)
-  const double *U;     // U_P sqrt(zeta) (2/sqrt(pi))^(1/2): pref = U_P U_Q / sqrt(zeta + eta)
+  const double *U;     // U_P sqrt(zeta) (2/sqrt(pi))^(1/2), already folded into E (kept for reference)
   const int *eoff;     // offset of the primitive pair's E block
-  const double *E;     // Hermite coefficients (Cartesian normalisation folded in)
+  const double *E;     // Hermite coefficients (Cartesian normalisation and U folded in)
   const double *Gp;    // primitive Schwarz factor G_[ab]; each pair's primitives sorted by it, descending
   const float *Gpf;    // the same rounded to FP32
   // FP32 copies for the mixed-precision path and the FP32 screening pre-test

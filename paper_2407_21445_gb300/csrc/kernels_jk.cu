@@ -215,9 +215,9 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
         const float rs = rsqrtf(PA.w + QC.w);
         const float alpha = (PA.w * QC.w) * (rs * rs);
         const float T = alpha * fmaf(X, X, fmaf(Y, Y, Z * Z));
-        boys_seeds_rt_f32<G>(a.boysf, T, dp.Uf[ip] * dp.Uf[jq] * rs, -2.0f * alpha, L, F, R0, gl);
+        boys_seeds_rt_f32<G>(a.boysf, T, rs, -2.0f * alpha, L, F, R0, gl);
       } else {
-        const PrimQuartet q = prim_quartet(dp.pz[ip], dp.pf[ip], dp.U[ip], dp.pz[jq], dp.pf[jq], dp.U[jq]);
+        const PrimQuartet q = prim_quartet(dp.pz[ip], dp.pf[ip], dp.pz[jq], dp.pf[jq]);
         FK_CHECK(q.T >= 0.0 && q.T == q.T && q.gi <= BOYS_NGRID - 1, 9, jq);
         X = q.X;
         Y = q.Y;
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(128) k_schwarz(DevPairs dp, const double *boys
       const PZ P4 = dp.pz[i];
       const float4 Pf = dp.pf[i];
       for (int j = pr.x; j < pr.x + pr.y; ++j) {
-        const PrimQuartet q = prim_quartet(P4, Pf, dp.U[i], dp.pz[j], dp.pf[j], dp.U[j]);
+        const PrimQuartet q = prim_quartet(P4, Pf, dp.pz[j], dp.pf[j]);
         boys_seeds_rt<32>(boys, q, L, F, R0, lane);
         __syncwarp();
         const double *R = hermite_r<32>(ct, L, q.X, q.Y, q.Z, F, R0, R1, lane, 0xffffffffu);

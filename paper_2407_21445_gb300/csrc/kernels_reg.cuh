@@ -137,12 +137,11 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &m
     if (prim_skip(a, mv, ps, ip, pk.x)) break;  // weaker bra primitives follow
     const PZ P4 = dp.pz[ip];
     const float4 Pf = dp.pf[ip];
-    const double UsP = dp.U[ip];
     double Y[NHAB * NCD];
     sfor<NHAB * NCD>([&](auto i) { Y[FK_CI(i)] = 0.0; });
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
       if (prim_skip(a, mv, ps, ip, jq)) break;  // weaker ket primitives follow
-      const PrimQuartet q = prim_quartet(P4, Pf, UsP, dp.pz[jq], dp.pf[jq], dp.U[jq]);
+      const PrimQuartet q = prim_quartet(P4, Pf, dp.pz[jq], dp.pf[jq]);
       double F[L + 1];
       boys_seeds<L>(a.boys, q, F);
       double R[NHL];
@@ -263,7 +262,6 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
     if (prim_skip(a, mv, ps, ip, pk.x)) break;
     const float4 PA = dp.paf[ip];
-    const float UP = dp.Uf[ip];
     float Y[NHAB * NCD];
     sfor<NHAB * NCD>([&](auto i) { Y[FK_CI(i)] = 0.0f; });
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
@@ -274,7 +272,7 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
       const float alpha = (PA.w * QC.w) * (rs * rs);
       const float T = alpha * fmaf(X, X, fmaf(Yd, Yd, Z * Z));
       float F[L + 1];
-      boys_seeds_f32<L>(a.boysf, T, UP * dp.Uf[jq] * rs, -2.0f * alpha, F);
+      boys_seeds_f32<L>(a.boysf, T, rs, -2.0f * alpha, F);
       float R[NHL];
       hermite_r_reg<L, float>(F, X, Yd, Z, R);
       const float *__restrict__ EQ = dp.Ef + dp.eoff[jq];
