@@ -66,12 +66,15 @@ void class_l(int c, int &la, int &lb) {
   lb = c - la * (la + 1) / 2;
 }
 
-// FP64 operation model of one primitive quartet (Boys Taylor, seeds, R
-// recursion, ket transform) and per bra primitive (bra transform).
+// FP64 operation model (an FMA counts 2) of one primitive quartet (Boys
+// Taylor, seeds, R recursion, ket transform) and per bra primitive (bra
+// transform).  Per primitive quartet: zeta + eta 1, 1/sqrt by one Newton-
+// Householder step 8, alpha 3, -2 alpha 1, P - Q 3, T 6, T_i - T 1 = 23;
+// per Boys order 7 Horner FMAs 14, seed scaling 1, power of -2 alpha 1 = 16.
 double flops_prim(int Lab, int L, int ck) {
   const ClassTables &ct = class_tables();
-  double f = 30.0;                  // alpha, T, prefactor
-  f += (L + 1) * (2.0 * 7 + 1.0);   // Taylor Horner + seed scaling
+  double f = 23.0;                  // alpha, T, 1/sqrt(zeta + eta)
+  f += (L + 1) * 16.0;              // Taylor Horner + seed scaling
   for (int n = L - 1; n >= 0; --n)  // Hermite recursion
     for (int e = 1; e < nherm(L - n); ++e) {
       const int t = ct.hvec[e][0], u = ct.hvec[e][1], w = ct.hvec[e][2];
