@@ -1,0 +1,34 @@
+"""bench.py's output contract, checked on CPU: the reference arm (the CPU
+oracle on a bounded sample) prints one JSON line with the keys a benchmark
+line carries, and the roofline helpers do their arithmetic."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "0",
+                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert "workload" in d["config"]
+
+
+def test_mixed_peak_fraction_arithmetic():
+    import bench
+    st = {"flops_model": 3.0e12, "flops_model_fp32": 1.0e12}
+    r = bench.mixed_peak_frac(st, 1000.0)  # one second
+    assert abs(r["fp64_achieved_tflops"] - 2.0) < 1e-12 and abs(r["fp32_achieved_tflops"] - 1.0) < 1e-12
+    assert abs(r["combined"] - (2.0 / bench.FP64_PEAK_TFLOPS + 1.0 / bench.FP32_PEAK_TFLOPS)) < 1e-12
+    assert abs(bench.FP64_PEAK_TFLOPS - 1.25856) < 1e-9
