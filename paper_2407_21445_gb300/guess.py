@@ -193,6 +193,16 @@ class LearnedGuess:
         self.sd = np.ones(NFEAT, dtype=np.float32)
         self.max_batch = max_batch
 
+    @classmethod
+    def load(cls, path: str, hidden: int = 128, max_batch: int = 8192):
+        """A trained network saved by train_guess (parameters and feature
+        normaliser)."""
+        z = np.load(path)
+        g = cls(hidden=hidden, max_batch=max_batch)
+        g.net.set_params(z["params"])
+        g.mu, g.sd = z["mu"].astype(np.float32), z["sd"].astype(np.float32)
+        return g
+
     def fit_normaliser(self, feats: np.ndarray):
         self.mu = feats.mean(0).astype(np.float32)
         self.sd = (feats.std(0) + 1e-3).astype(np.float32)

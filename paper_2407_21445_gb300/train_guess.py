@@ -25,13 +25,18 @@ from . import guess as G
 from .scf import RHF, sad_guess
 
 
+def split(n: int = 500, ntrain: int = 400, seed: int = 0):
+    """The seeded train / held-out split of the n conformations."""
+    rng = np.random.Generator(np.random.PCG64(50_000 + seed))
+    order = rng.permutation(n)
+    return sorted(order[:ntrain].tolist()), sorted(order[ntrain:].tolist())
+
+
 def run(n: int, ntrain: int, out: str, epochs: int, seed: int = 0, tau: float = 1e-10, log=print):
     os.makedirs(out, exist_ok=True)
     table = molgen.basis_set("dz", seed)
     mols = molgen.scf_conformations(n, seed)
-    rng = np.random.Generator(np.random.PCG64(50_000 + seed))
-    order = rng.permutation(n)
-    train_idx, test_idx = sorted(order[:ntrain].tolist()), sorted(order[ntrain:].tolist())
+    train_idx, test_idx = split(n, ntrain, seed)
     rec = {}
     feats, targs, masks = [], [], []
     t0 = time.time()
@@ -104,13 +109,8 @@ def sensitivity(params: str, out: str, n: int = 500, ntrain: int = 400, nmol: in
     os.makedirs(out, exist_ok=True)
     table = molgen.basis_set("dz", seed)
     mols = molgen.scf_conformations(n, seed)
-    rng = np.random.Generator(np.random.PCG64(50_000 + seed))
-    order = rng.permutation(n)
-    test_idx = sorted(order[ntrain:].tolist())[:nmol]
-    z = np.load(params)
-    lg = G.LearnedGuess(hidden=128, max_batch=8192, seed=seed)
-    lg.net.set_params(z["params"])
-    lg.mu, lg.sd = z["mu"], z["sd"]
+    test_idx = split(n, ntrain, seed)[1][:nmol]
+    lg = G.LearnedGuess.load(params)
     rows = []
     for i in test_idx:
         mol = mols[i]
