@@ -115,6 +115,8 @@ def lib() -> ctypes.CDLL:
             L.fock_hermite_count.restype = i
             L.fock_hermite_e.argtypes = [i, i, d, p, d, p, p]
             L.fock_hermite_e.restype = i
+            L.fock_build_jk_noalloc.argtypes = [p, p, d, p, p, p]
+            L.fock_build_jk_noalloc.restype = i
             L.fock_opts_size.argtypes = []
             L.fock_opts_size.restype = i
             L.fock_autotune.argtypes = [p, i, p, ctypes.POINTER(fock_opts), d, i, p, ctypes.POINTER(fock_opts), p,
@@ -223,6 +225,16 @@ def fock_build_jk(handle, D, schwarz_thresh: float, J, K, stream=None):
     _check(rc, "fock_build_jk")
 
 
+def fock_build_jk_noalloc(handle, D, schwarz_thresh: float, J, K, stream=None):
+    rc = lib().fock_build_jk_noalloc(handle, _tensor_ptr(D, "D"), float(schwarz_thresh), _tensor_ptr(J, "J"),
+                                     _tensor_ptr(K, "K"), _stream_handle(stream))
+    _check(rc, "fock_build_jk_noalloc")
+
+
+def fock_opts_size() -> int:
+    return int(lib().fock_opts_size())
+
+
 def fock_build_jk_batched(handles, Ds, schwarz_thresh: float, Js, Ks, stream=None):
     n = len(handles)
     H = (ctypes.c_void_p * n)(*[h.value for h in handles])
@@ -323,57 +335,96 @@ def _f32_ptr(t, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+# --- atom-pair MLP (fock_mlp_*), one wrapper per entry point ---------------
+
+def fock_mlp_create(nin: int, nhidden: int, nout: int, max_batch: int, seed: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib().fock_mlp_create(nin, nhidden, nout, max_batch, seed, ctypes.byref(h)), "fock_mlp_create")
+    return h
+
+
+def fock_mlp_free(handle):
+    _check(lib().fock_mlp_free(handle), "fock_mlp_free")
+
+
+def fock_mlp_num_params(handle) -> int:
+    return int(lib().fock_mlp_num_params(handle))
+
+
+def fock_mlp_get_params(handle, params: np.ndarray | None, grads: np.ndarray | None):
+    """Copies the FP32 master parameters and/or gradients into the given host arrays."""
+    _check(lib().fock_mlp_get_params(handle, None if params is None else _np_ptr(params),
+                                     None if grads is None else _np_ptr(grads)), "fock_mlp_get_params")
+
+
+def fock_mlp_set_params(handle, params: np.ndarray):
+    _check(lib().fock_mlp_set_params(handle, _np_ptr(params)), "fock_mlp_set_params")
+
+
+def fock_mlp_forward(handle, X, n: int, Y, stream=None):
+    _check(lib().fock_mlp_forward(handle, _f32_ptr(X, "X"), n, _f32_ptr(Y, "Y"), _stream_handle(stream)),
+           "fock_mlp_forward")
+
+
+def fock_mlp_loss_backward(handle, X, T, mask, n: int, norm: float, stream=None) -> float:
+    out = np.zeros(1, dtype=np.float32)
+    _check(lib().fock_mlp_loss_backward(handle, _f32_ptr(X, "X"), _f32_ptr(T, "T"),
+                                        None if mask is None else _f32_ptr(mask, "mask"), n, float(norm),
+                                        _np_ptr(out), _stream_handle(stream)), "fock_mlp_loss_backward")
+    return float(out[0])
+
+
+def fock_mlp_step(handle, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+    _check(lib().fock_mlp_step(handle, lr, beta1, beta2, eps, weight_decay, _stream_handle(stream)), "fock_mlp_step")
+
+
+def fock_mlp_zero_grad(handle, stream=None):
+    _check(lib().fock_mlp_zero_grad(handle, _stream_handle(stream)), "fock_mlp_zero_grad")
+
+
 class MLP:
     """The library's atom-pair MLP (fock_mlp_*): BF16 weights, FP32 accumulation."""
 
     def __init__(self, nin: int, nhidden: int, nout: int, max_batch: int, seed: int = 0):
         self.nin, self.nhidden, self.nout, self.max_batch = nin, nhidden, nout, max_batch
-        h = ctypes.c_void_p()
-        _check(lib().fock_mlp_create(nin, nhidden, nout, max_batch, seed, ctypes.byref(h)), "fock_mlp_create")
-        self.handle = h
-        self.nparam = int(lib().fock_mlp_num_params(h))
+        self.handle = fock_mlp_create(nin, nhidden, nout, max_batch, seed)
+        self.nparam = fock_mlp_num_params(self.handle)
 
     def params(self):
         p = np.zeros(self.nparam, dtype=np.float32)
-        _check(lib().fock_mlp_get_params(self.handle, _np_ptr(p), None), "fock_mlp_get_params")
+        fock_mlp_get_params(self.handle, p, None)
         return p
 
     def grads(self):
         g = np.zeros(self.nparam, dtype=np.float32)
-        _check(lib().fock_mlp_get_params(self.handle, None, _np_ptr(g)), "fock_mlp_get_params")
+        fock_mlp_get_params(self.handle, None, g)
         return g
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
         assert p.size == self.nparam
-        _check(lib().fock_mlp_set_params(self.handle, _np_ptr(p)), "fock_mlp_set_params")
+        fock_mlp_set_params(self.handle, p)
 
     def forward(self, X, Y=None, stream=None):
         import torch
         if Y is None:
             Y = torch.empty((X.shape[0], self.nout), dtype=torch.float32, device=X.device)
-        _check(lib().fock_mlp_forward(self.handle, _f32_ptr(X, "X"), X.shape[0], _f32_ptr(Y, "Y"),
-                                      _stream_handle(stream)), "fock_mlp_forward")
+        fock_mlp_forward(self.handle, X, X.shape[0], Y, stream)
         return Y
 
     def loss_backward(self, X, T, mask=None, norm=None, stream=None) -> float:
-        out = np.zeros(1, dtype=np.float32)
         norm = float(mask.sum()) if (norm is None and mask is not None) else float(norm or T.numel())
-        _check(lib().fock_mlp_loss_backward(self.handle, _f32_ptr(X, "X"), _f32_ptr(T, "T"),
-                                            None if mask is None else _f32_ptr(mask, "mask"), X.shape[0], norm,
-                                            _np_ptr(out), _stream_handle(stream)), "fock_mlp_loss_backward")
-        return float(out[0])
+        return fock_mlp_loss_backward(self.handle, X, T, mask, X.shape[0], norm, stream)
 
     def step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
-        _check(lib().fock_mlp_step(self.handle, lr, beta1, beta2, eps, weight_decay, _stream_handle(stream)),
-               "fock_mlp_step")
+        fock_mlp_step(self.handle, lr, beta1, beta2, eps, weight_decay, stream)
 
     def zero_grad(self, stream=None):
-        _check(lib().fock_mlp_zero_grad(self.handle, _stream_handle(stream)), "fock_mlp_zero_grad")
+        fock_mlp_zero_grad(self.handle, stream)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
-            lib().fock_mlp_free(self.handle)
+            fock_mlp_free(self.handle)
             self.handle = None
 
     def __del__(self):

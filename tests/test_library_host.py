@@ -30,6 +30,12 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, n), n
 
 
+def test_binding_has_every_entry_point():
+    """The Python binding offers each C entry point under its own name."""
+    for n in fb.declared_symbols():
+        assert callable(getattr(fb, n, None)), n
+
+
 def test_status_strings():
     for i, name in enumerate(fb.STATUS_NAMES):
         assert fk.fock_status_string(i) == name
