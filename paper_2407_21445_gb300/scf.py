@@ -5,7 +5,7 @@ J and K come from libfock.so; the one-electron integrals from
 fock_one_electron; the small dense linear algebra (canonical
 orthogonalisation, DIIS, FP64 eigendecomposition) uses torch.linalg on the
 GPU.  Initial guesses: superposition of atomic densities (SAD) or a density
-supplied by the caller (the learned guess of mlp.py).
+supplied by the caller (the learned guess of guess.py).
 """
 from __future__ import annotations
 
