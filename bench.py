@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--tune-cache", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                                          "paper_2407_21445_gb300", "_build", "tune_cache.json"))
     ap.add_argument("--tune-nmol", type=int, default=2, help="--config 3: molecules the schedule is measured on")
+    ap.add_argument("--write-traffic", metavar="NCU_CSV", default=None,
+                    help="write profiles/jk_c20h42_traffic.json from an ncu CSV of one build's launches "
+                         "(dram__bytes_read.sum, dram__bytes_write.sum) and exit")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the headline leg (mixed: FP32 below --fp32-cutoff)")
     return ap.parse_args()
@@ -139,6 +142,26 @@ def profile_traffic(kernel_src_hash: str):
     if d.get("kernel_source_sha256") != kernel_src_hash:
         return None
     return d.get("dram_bytes_per_build")
+
+
+def write_traffic(csv_path: str, command: str):
+    """Sum the DRAM bytes of one build's launches from an ncu --csv log and
+    record them with the kernel-source hash they belong to."""
+    import csv
+    import io
+    rows = [l for l in open(csv_path).read().splitlines() if l.startswith('"')]
+    per = {}
+    for r in csv.DictReader(io.StringIO("\n".join(rows))):
+        per.setdefault(r["ID"], {})[r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
+    rd = sum(v.get("dram__bytes_read.sum", 0.0) for v in per.values())
+    wr = sum(v.get("dram__bytes_write.sum", 0.0) for v in per.values())
+    t = sum(v.get("gpu__time_duration.sum", 0.0) for v in per.values())
+    d = {"kernel_source_sha256": kernel_hash(), "launches": len(per), "dram_bytes_read": rd, "dram_bytes_write": wr,
+         "dram_bytes_per_build": rd + wr, "serialised_time_ns": t, "command": command}
+    out = os.path.join(ROOT, "profiles", "jk_c20h42_traffic.json")
+    with open(out, "w") as f:
+        json.dump(d, f, indent=1)
+    return d
 
 
 def kernel_hash():
@@ -341,6 +364,12 @@ def run_batched(args, fk, torch, dev, stream, world, rank, dist):
 
 def main():
     args = parse()
+    if args.write_traffic:
+        print(json.dumps(write_traffic(args.write_traffic, "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,"
+                                       "dram__bytes_write.sum --clock-control none -k regex:'k_reg|k_jk|k_dprep|k_symm' "
+                                       "-s 81 -c 27 --csv --log-file traffic_c20.csv python bench.py --steps 2 "
+                                       "--warmup 3 --no-cpu-baseline --no-mixed-leg --no-autotune")))
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
