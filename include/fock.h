@@ -217,10 +217,11 @@ FOCK_API fock_status fock_build_jk_batched(const fock_shellpairs *const *bases, 
  *   out[1] Cartesian ERIs in those quartets (throughput unit)
  *   out[2] quartets also passing the density-weighted test (evaluated)
  *   out[3] Cartesian ERIs in evaluated quartets
- *   out[4] primitive quartets evaluated
- *   out[5] modelled FP64 floating-point operations of the evaluated work
- *          (per-class Hermite-scheme counts: Boys, R recursion, ket and bra
- *          Hermite transforms, digestion)
+ *   out[4] primitive quartets evaluated (after primitive-quartet screening)
+ *   out[5] modelled FP64 floating-point operations of the evaluated work, an
+ *          FMA counting 2 (per-class Hermite-scheme counts: primitive-quartet
+ *          setup, Boys, R recursion, ket and bra Hermite transforms,
+ *          digestion)
  *   out[6] primitive pairs kept after pruning
  *   out[7] contracted pairs kept
  *   out[8] evaluated quartets taken by the FP32 path (mixed precision)
