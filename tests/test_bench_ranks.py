@@ -3,7 +3,6 @@ gets the slowest rank's time, as the whole-job throughput requires."""
 import os
 import socket
 
-import pytest
 import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp

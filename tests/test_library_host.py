@@ -8,7 +8,6 @@ import math
 import os
 
 import numpy as np
-import pytest
 
 import molgen
 import oracle

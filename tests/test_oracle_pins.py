@@ -1,7 +1,6 @@
 """Pins of the CPU oracle against facts fixed by the paper and by mathematics,
 independent of the oracle's own code paths (closed forms, quadrature,
 identities, brute force).  None of these needs a GPU."""
-import itertools
 import math
 
 import numpy as np
