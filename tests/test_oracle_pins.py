@@ -124,12 +124,17 @@ def _quadrature_eri(la, lb, lc, ld, a, A, b, B, c, C, d, D, nt=400):
     ws = 0.5 * ws
     ts = scale * s / (1 - s)
     dts = scale / (1 - s) ** 2
-    la_c, lb_c, lc_c, ld_c = (cart_list(l) for l in (la, lb, lc, ld))
-    out = np.zeros((len(la_c), len(lb_c), len(lc_c), len(ld_c)))
-    # per t, per axis, moments M[ax][i][j][k][m] = int int (x1-A)^i (x1-B)^j (x2-C)^k (x2-D)^m e^{-Q}
-    acc = np.zeros_like(out)
+    la_c, lb_c, lc_c, ld_c = (np.array(cart_list(l)) for l in (la, lb, lc, ld))
+    # component exponents of every (ia, ib, ic, id) combination, per axis
+    ua = la_c[:, None, None, None, :]
+    ub = lb_c[None, :, None, None, :]
+    uc = lc_c[None, None, :, None, :]
+    ud = ld_c[None, None, None, :, :]
+    shape = (len(la_c), len(lb_c), len(lc_c), len(ld_c))
+    idx = [np.broadcast_to(x, shape + (3,)) for x in (ua, ub, uc, ud)]
+    acc = np.zeros(shape)
     for t, wt, dt in zip(ts, ws, dts):
-        mom = []
+        val = np.ones(shape)
         for ax in range(3):
             # quadratic form p(x1-P)^2 + q(x2-Q)^2 + t^2 (x1-x2)^2
             M = np.array([[p + t * t, -t * t], [-t * t, q + t * t]])
@@ -140,28 +145,20 @@ def _quadrature_eri(la, lb, lc, ld, a, A, b, B, c, C, d, D, nt=400):
             X1 = m0[0] + V[0, 0] * Y1 / math.sqrt(lam[0]) + V[0, 1] * Y2 / math.sqrt(lam[1])
             X2 = m0[1] + V[1, 0] * Y1 / math.sqrt(lam[0]) + V[1, 1] * Y2 / math.sqrt(lam[1])
             jac = math.exp(-c0) / math.sqrt(lam[0] * lam[1])
-            mm = {}
-            for i in range(la + 1):
-                for j in range(lb + 1):
-                    for k in range(lc + 1):
-                        for m in range(ld + 1):
-                            f = (X1 - A[ax]) ** i * (X1 - B[ax]) ** j * (X2 - C[ax]) ** k * (X2 - D[ax]) ** m
-                            mm[(i, j, k, m)] = jac * np.sum(W * f)
-            mom.append(mm)
-        for ia, u in enumerate(la_c):
-            for ib, v in enumerate(lb_c):
-                for ic, w_ in enumerate(lc_c):
-                    for id_, z in enumerate(ld_c):
-                        val = 1.0
-                        for ax in range(3):
-                            val *= mom[ax][(u[ax], v[ax], w_[ax], z[ax])]
-                        acc[ia, ib, ic, id_] += wt * dt * val
+            # moments[i, j, k, m] = int int (x1-A)^i (x1-B)^j (x2-C)^k (x2-D)^m e^{-Q}
+            pa = (X1 - A[ax])[None] ** np.arange(la + 1)[:, None, None]
+            pb = (X1 - B[ax])[None] ** np.arange(lb + 1)[:, None, None]
+            pc = (X2 - C[ax])[None] ** np.arange(lc + 1)[:, None, None]
+            pd = (X2 - D[ax])[None] ** np.arange(ld + 1)[:, None, None]
+            mom = jac * np.einsum("xy,ixy,jxy,kxy,mxy->ijkm", W, pa, pb, pc, pd)
+            val = val * mom[idx[0][..., ax], idx[1][..., ax], idx[2][..., ax], idx[3][..., ax]]
+        acc += wt * dt * val
     return pref * 2 / math.sqrt(math.pi) * acc
 
 
 @pytest.mark.parametrize("ls", [(0, 0, 0, 0), (1, 0, 0, 0), (1, 1, 0, 0), (1, 0, 1, 0), (1, 1, 1, 1),
                                 (2, 0, 1, 0), (2, 1, 2, 0), (2, 2, 1, 1), (2, 2, 2, 2), (3, 0, 1, 0),
-                                (3, 1, 2, 0), (3, 3, 0, 0)])
+                                (3, 1, 2, 0), (3, 3, 0, 0), (3, 3, 2, 2), (3, 3, 3, 3)])
 def test_eri_brute_force_quadrature(ls, rng):
     la, lb, lc, ld = ls
     a, b, c, d = rng.uniform(0.3, 3.0, 4)
@@ -423,6 +420,160 @@ def test_one_electron_invariances(rng):
     assert np.abs(T1 - T1.T).max() < 1e-12 and np.abs(V1 - V1.T).max() < 1e-11
     # the kinetic energy operator is positive definite on independent functions
     assert np.linalg.eigvalsh(T1).min() > 0
+
+
+def _dfact(n):
+    return 1 if n <= 0 else n * _dfact(n - 2)
+
+
+def _one_electron_quadrature(la, a, A, lb, b, B, Zs, Cs, nt=400):
+    """Brute force S, T, V between two primitive Cartesian shells, normalised
+    to unit self-overlap, without the Boys function or any recurrence.
+    Per axis the 1-D integrals of polynomial x Gaussian are exact by
+    Gauss-Hermite after completing the square; T applies the second derivative
+    to the ket factor (-1/2 nabla^2); 1/|r-C| = 2/sqrt(pi) int_0^inf
+    exp(-t^2 |r-C|^2) dt with the t integral by mapped Gauss-Legendre."""
+    gx, gw = np.polynomial.hermite.hermgauss(16)
+
+    def line(i, j, ax, t2=0.0, c=0.0, deriv=False):
+        g = a + b + t2
+        x0 = (a * A[ax] + b * B[ax] + t2 * c) / g
+        k0 = a * A[ax] ** 2 + b * B[ax] ** 2 + t2 * c * c - g * x0 * x0
+        x = x0 + gx / math.sqrt(g)
+        xa, xb = x - A[ax], x - B[ax]
+        if deriv:  # d^2/dx^2 of (x-B)^j exp(-b (x-B)^2), Gaussian factor kept apart
+            fb = 4 * b * b * xb ** (j + 2) - 2 * b * (2 * j + 1) * xb ** j
+            if j >= 2:
+                fb = fb + j * (j - 1) * xb ** (j - 2)
+        else:
+            fb = xb ** j
+        return math.exp(-k0) / math.sqrt(g) * np.sum(gw * xa ** i * fb)
+
+    ca, cb = cart_list(la), cart_list(lb)
+
+    def norm(l, e, X, u):
+        g = 2 * e
+        return math.sqrt(np.prod([np.sum(gw * (gx / math.sqrt(g)) ** (2 * u[k])) / math.sqrt(g) for k in range(3)]))
+
+    na = [norm(la, a, A, u) for u in ca]
+    nb = [norm(lb, b, B, v) for v in cb]
+    S = np.zeros((len(ca), len(cb)))
+    T = np.zeros_like(S)
+    V = np.zeros_like(S)
+    s, ws = np.polynomial.legendre.leggauss(nt)
+    s = 0.5 * (s + 1)
+    ws = 0.5 * ws
+    scale = math.sqrt(a + b)
+    ts, dts = scale * s / (1 - s), scale / (1 - s) ** 2
+    for i, u in enumerate(ca):
+        for j, v in enumerate(cb):
+            o = [line(u[k], v[k], k) for k in range(3)]
+            d2 = [line(u[k], v[k], k, deriv=True) for k in range(3)]
+            S[i, j] = np.prod(o)
+            T[i, j] = -0.5 * (d2[0] * o[1] * o[2] + o[0] * d2[1] * o[2] + o[0] * o[1] * d2[2])
+            acc = 0.0
+            for Z, C in zip(Zs, Cs):
+                f = [np.prod([line(u[k], v[k], k, t * t, C[k]) for k in range(3)]) for t in ts]
+                acc -= Z * 2 / math.sqrt(math.pi) * np.sum(ws * dts * np.array(f))
+            V[i, j] = acc
+            S[i, j] /= na[i] * nb[j]
+            T[i, j] /= na[i] * nb[j]
+            V[i, j] /= na[i] * nb[j]
+    return S, T, V
+
+
+@pytest.mark.parametrize("la,lb", [(2, 0), (2, 1), (2, 2), (3, 1), (3, 2), (3, 3)])
+def test_one_electron_brute_force_quadrature(la, lb, rng):
+    """S, T, V of d and f shells (h = T + V, Sec. 2.2) against quadrature that
+    shares no step with the oracle's Obara-Saika recurrences."""
+    a, b = rng.uniform(0.3, 3.0, 2)
+    A, B = rng.uniform(-1.0, 1.0, (2, 3))
+    Zs = [1.0, 6.0]
+    Cs = [rng.uniform(-1.5, 1.5, 3), rng.uniform(-1.5, 1.5, 3)]
+    Sq, Tq, Vq = _one_electron_quadrature(la, a, A, lb, b, B, Zs, Cs)
+    bas = molgen.single_shell_basis([(la, A, [a], [1.0]), (lb, B, [b], [1.0])])
+    na = oracle.ncart(la)
+    S = oracle.overlap(bas)[:na, na:]
+    T = oracle.kinetic(bas)[:na, na:]
+    V = oracle.nuclear(bas, Zs, Cs)[:na, na:]
+    for ref, val in ((Sq, S), (Tq, T), (Vq, V)):
+        assert np.abs(val - ref).max() <= 1e-11 * np.abs(ref).max(), np.abs(val - ref).max()
+
+
+def test_one_electron_harmonic_d_f_closed_forms():
+    """xy, xz, yz and xyz times exp(-a r^2) are pure solid harmonics (l = 2, 3):
+    on a nucleus of charge Z, T = (2l+3) a / 2 and
+    <1/r> = 2^(l+1) l! sqrt(2a) / ((2l+1)!! sqrt(pi))."""
+    C = np.array([-0.4, 0.25, 0.6])
+    for a in (0.3, 2.0, 11.0):
+        for l, comps in ((2, (1, 2, 4)), (3, (4,))):
+            bas = molgen.single_shell_basis([(l, C, [a], [1.0])])
+            T = oracle.kinetic(bas)
+            V = oracle.nuclear(bas, [2.5], [C])
+            r1 = 2 ** (l + 1) * math.factorial(l) * math.sqrt(2 * a) / (_dfact(2 * l + 1) * math.sqrt(math.pi))
+            for c in comps:
+                assert abs(T[c, c] - (2 * l + 3) * a / 2) < 1e-13 * a
+                assert abs(V[c, c] + 2.5 * r1) < 1e-13 * r1
+
+
+def _rotation_matrix_cart(ls, Rm):
+    """M with g_mu = sum_k M[mu, k] phi'_k: a normalised Cartesian function of
+    the original molecule, rotated by Rm, expanded in the normalised Cartesian
+    functions at the rotated centre.  x^u y^v z^w becomes the product of the
+    rotated coordinates (Rm^T s)_i; each monomial's unit-norm factor is
+    proportional to 1 / sqrt((2u-1)!! (2v-1)!! (2w-1)!!) within a shell."""
+    blocks = []
+    for l in ls:
+        comps = cart_list(int(l))
+        pos = {c: i for i, c in enumerate(comps)}
+        nf = [1.0 / math.sqrt(_dfact(2 * c[0] - 1) * _dfact(2 * c[1] - 1) * _dfact(2 * c[2] - 1)) for c in comps]
+        Mb = np.zeros((len(comps), len(comps)))
+        for i, u in enumerate(comps):
+            poly = {(0, 0, 0): 1.0}
+            for ax in range(3):
+                for _ in range(u[ax]):
+                    nxt = {}
+                    for e, cf in poly.items():
+                        for k in range(3):  # (Rm^T s)_ax = sum_k Rm[k, ax] s_k
+                            e2 = list(e)
+                            e2[k] += 1
+                            nxt[tuple(e2)] = nxt.get(tuple(e2), 0.0) + cf * Rm[k, ax]
+                    poly = nxt
+            for e, cf in poly.items():
+                Mb[i, pos[e]] += nf[i] * cf / nf[pos[e]]
+        blocks.append(Mb)
+    n = sum(b.shape[0] for b in blocks)
+    M = np.zeros((n, n))
+    o = 0
+    for b in blocks:
+        M[o:o + b.shape[0], o:o + b.shape[0]] = b
+        o += b.shape[0]
+    return M
+
+
+def test_rotation_covariance_spdf(rng):
+    """1/r12 and the kinetic and nuclear operators are rotation invariant, so
+    for the molecule rotated by Rm, (mn|ls) = sum M M M M (ab|cd)' and
+    J(D) = M J'(M^T D M) M^T, K likewise, S = M S' M^T, etc. (Sec. 2.2
+    integrals over Cartesian d and f functions)."""
+    ls = [0, 1, 2, 3, 2, 1]
+    bas = molgen.random_shells(rng, ls, spread=1.4, kmax=2)
+    Rm = molgen.random_rotation(rng)
+    bas2 = dict(bas)
+    bas2["center"] = bas["center"] @ Rm.T
+    M = _rotation_matrix_cart(bas["l"], Rm)
+    n = oracle.nbf(bas)
+    D = rng.uniform(-1, 1, (n, n))
+    D = D + D.T
+    J, K = oracle.jk(bas, D, mode=oracle.SCREEN_NONE, eps_prune=0.0)
+    J2, K2 = oracle.jk(bas2, M.T @ D @ M, mode=oracle.SCREEN_NONE, eps_prune=0.0)
+    assert np.abs(M @ J2 @ M.T - J).max() < 1e-11 * np.abs(J).max()
+    assert np.abs(M @ K2 @ M.T - K).max() < 1e-11 * np.abs(K).max()
+    Zs = np.array([1.0, 8.0, 6.0])
+    at = rng.uniform(-2, 2, (3, 3))
+    for f1, f2 in ((oracle.overlap(bas), oracle.overlap(bas2)), (oracle.kinetic(bas), oracle.kinetic(bas2)),
+                   (oracle.nuclear(bas, Zs, at), oracle.nuclear(bas2, Zs, at @ Rm.T))):
+        assert np.abs(M @ f2 @ M.T - f1).max() < 1e-12 * np.abs(f1).max()
 
 
 # --------------------------------------------------------------------------
