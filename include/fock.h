@@ -78,8 +78,9 @@ typedef struct {
 /* Options; pass NULL for the defaults shown. */
 typedef struct {
   int32_t precision;    /* FOCK_FP64 (default) or FOCK_MIXED                     */
-  double fp32_cutoff;   /* mixed path: quartets with G_ab G_cd Dmax below this
-                           bound are evaluated in FP32 (default 1e-5)           */
+  double fp32_cutoff;   /* mixed path: quartets with G_ab G_cd Dmax, and
+                           primitive quartets with G_[ab] G_[cd] Dmax, below
+                           this bound are evaluated in FP32 (default 1e-5)      */
   double prune_eps;     /* primitive screening (Sec. 3.2, 3.3): primitive pair
                            [ab] dropped when G_[ab] Gmax < tau * prune_eps, and
                            inside a quartet that passes, primitive quartet
@@ -155,7 +156,9 @@ FOCK_API int32_t fock_nbasis(const fock_shellpairs *sp);
  * such a quartet, a primitive quartet [ab|cd] is skipped when
  * G_[ab] G_[cd] Dmax < schwarz_thresh * prune_eps (Sec. 3.2, 3.3).  With
  * precision FOCK_MIXED, a quartet whose bound is below fp32_cutoff is
- * evaluated in FP32 and its contributions are accumulated in FP64.
+ * evaluated in FP32, and inside a quartet at or above it every primitive
+ * quartet whose own bound G_[ab] G_[cd] Dmax is below fp32_cutoff is
+ * evaluated in FP32; all contributions are accumulated in FP64.
  *   D: device, N x N row-major float64, symmetric (read).
  *   J, K: device, N x N row-major float64 (overwritten).
  *   schwarz_thresh >= the value the handle was built with.
@@ -178,16 +181,20 @@ FOCK_API fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, d
  * they run -- services that reserve their whole memory budget at start-up,
  * applications whose allocator policy forbids the CUDA runtime's
  * stream-ordered pool, real-time loops where an allocation could stall.
- * Arguments, layouts, errors and results are those of fock_build_jk.  The
- * per-call scratch (shell-block density maxima and work counters) lives in a
- * fixed 4 MiB array inside the library, which every GPU that loads the
- * library keeps until the process exits; handles with more than 724 shells
- * do not fit and return FOCK_ERR_INVALID_ARG without doing any work.  The
- * first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call uses the same array: calls whose GPU work can overlap (other
- * streams, other host threads) race on it and must be serialised by the
- * caller.  No cudaMalloc, cudaMallocAsync or cudaFree is called.
+ * Arguments, layouts, errors and results are those of fock_build_jk, in both
+ * precisions (the same kernels run with the same inputs).  The per-call
+ * scratch lives in a fixed 4 MiB array inside the library, which every GPU
+ * that loads the library keeps until the process exits.  A call needs
+ * 12 nshell^2 bytes (shell-block density maxima in FP64 and FP32), plus
+ * 4 N^2 bytes with FOCK_MIXED (the FP32 copy of D), plus a few hundred bytes
+ * of work counters: FP64 handles fit up to 591 shells.  Handles that do not
+ * fit return FOCK_ERR_INVALID_ARG without doing any work.  Every call looks
+ * up the array's device address (cudaGetSymbolAddress); the first call on
+ * each device also loads the library's device code there, so make that first
+ * call before any stream capture.  Every call uses the same array: calls
+ * whose GPU work can overlap (other streams, other host threads) race on it
+ * and must be serialised by the caller.  No cudaMalloc, cudaMallocAsync or
+ * cudaFree is called.
  */
 FOCK_API fock_status fock_build_jk_noalloc(const fock_shellpairs *sp, const double *D, double schwarz_thresh,
                                            double *J, double *K, cudaStream_t stream);
@@ -225,7 +232,9 @@ FOCK_API fock_status fock_build_jk_batched(const fock_shellpairs *const *bases, 
  *   out[6] primitive pairs kept after pruning
  *   out[7] contracted pairs kept
  *   out[8] evaluated quartets taken by the FP32 path (mixed precision)
- *   out[9] modelled floating-point operations of those FP32 quartets
+ *   out[9] modelled floating-point operations run in FP32: those FP32
+ *          quartets, plus the primitive quartets below the cutoff inside the
+ *          FP64 ones (mixed precision)
  * D: host, N x N row-major float64.  Synchronous.
  */
 FOCK_API fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host,

@@ -221,6 +221,8 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
 }  // namespace
 
 namespace fk {
+fock_status cuda_status(cudaError_t e, const char *where) { return to_status(e, where); }
+bool sync_each_launch() { return sync_check(); }
 fock_status validate_basis(const fock_basis_desc *d) { return validate(d); }
 void normalised_coefs(const fock_basis_desc *d, int s, double *out) { norm_coefs(d, s, out); }
 fock_status upload_staging(const Staging &st, const std::vector<Unit> &units, void **base, DevPairs &dp,
@@ -604,6 +606,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     tier.reg_ck = keys[ki].ck;
     tier.sb = keys[ki].sb;
     tier.tag = keys[ki].tag;
+    tier.mixed = (o.precision == FOCK_MIXED && o.fp32_cutoff > 0.0) ? 1 : 0;
     int stride = 1;
     const int chunk = (32 / tier.G) * 8;
     const size_t first = all_units.size();
@@ -785,25 +788,38 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
       const int2 pb = sp->h_prim[P], pk = sp->h_prim[Q];
       const double *Gp = sp->host.Gp.data();
       const double teps = sp->prune_eps > 0.0 ? tau * sp->prune_eps : 0.0;
-      double np = 0.0, nbra = 0.0;
+      // mixed precision: inside a quartet at or above the cutoff, primitive
+      // quartets whose own bound is below it run in FP32 (the kernels decide
+      // on FP32 copies of the same numbers)
+      const bool split = mixed && !(g * dm < sp->opts.fp32_cutoff);
+      double np = 0.0, nbra = 0.0, np32 = 0.0, nbra32 = 0.0, nbra64 = 0.0;
       for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
-        int n = 0;
+        int n = 0, n32 = 0;
         for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
-          if (Gp[ip] * Gp[jq] * dm < teps) break;
+          const double x = Gp[ip] * Gp[jq] * dm;
+          if (x < teps) break;
           ++n;
+          if (split && x < sp->opts.fp32_cutoff) ++n32;
         }
         if (n == 0) break;
         np += n;
         nbra += 1;
+        np32 += n32;
+        if (n32 > 0) nbra32 += 1;
+        if (n > n32) nbra64 += 1;
       }
       pq += np;
       const FlopTable &ft = flop_table();
-      const double f = np * ft.prim[sp->h_cls[P]][sp->h_cls[Q]] + nbra * ft.bra[sp->h_cls[P]][sp->h_cls[Q]] +
-                       12.0 * ne;
-      fl += f;
+      const double fp = ft.prim[sp->h_cls[P]][sp->h_cls[Q]], fb = ft.bra[sp->h_cls[P]][sp->h_cls[Q]];
       if (mixed && g * dm < sp->opts.fp32_cutoff) {
+        const double f = np * fp + nbra * fb + 12.0 * ne;
+        fl += f;
         q32 += 1;
         fl32 += f;
+      } else {
+        const double f32 = np32 * fp + nbra32 * fb;
+        fl += (np - np32) * fp + nbra64 * fb + 12.0 * ne + f32;
+        fl32 += f32;
       }
     }
   }

@@ -69,10 +69,7 @@ std::mutex g_mu;
 std::vector<BatchPlan *> g_plans;  // most recent last
 constexpr size_t kMaxPlans = 4;
 
-fock_status cuda_status(cudaError_t e) {
-  if (e == cudaSuccess) return FOCK_OK;
-  return e == cudaErrorMemoryAllocation ? FOCK_ERR_OOM : FOCK_ERR_CUDA;
-}
+fock_status batch_status(cudaError_t e) { return cuda_status(e, "fock_build_jk_batched"); }
 
 bool same_opts(const fock_shellpairs *a, const fock_shellpairs *b) {
   return a->tau_build == b->tau_build && a->opts.precision == b->opts.precision &&
@@ -178,7 +175,7 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
   cudaError_t ce = cudaStreamCreateWithFlags(&bp->st, cudaStreamNonBlocking);
   if (ce != cudaSuccess) {
     delete bp;
-    return cuda_status(ce);
+    return batch_status(ce);
   }
   Unit *d_units = nullptr;
   fock_status s = upload_staging(m, all, &bp->d_block, bp->dev, &d_units, nullptr, bp->st);
@@ -193,7 +190,7 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
     ce = configure_tier(bp->tiers[t]);
     if (ce != cudaSuccess) {
       delete bp;
-      return cuda_status(ce);
+      return batch_status(ce);
     }
   }
   // table, prefixes and scratch in one allocation
@@ -218,7 +215,7 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
   ce = cudaMalloc(&aux, off);
   if (ce != cudaSuccess) {
     delete bp;
-    return cuda_status(ce);
+    return batch_status(ce);
   }
   bp->d_aux = aux;
   bp->d_mt = (MolEntry *)(aux + o_mt);
@@ -245,7 +242,7 @@ fock_status build_plan(const fock_shellpairs *const *bases, int nmol, BatchPlan 
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(bp->st);
   if (ce != cudaSuccess) {
     delete bp;
-    return cuda_status(ce);
+    return batch_status(ce);
   }
   *out = bp;
   return FOCK_OK;
@@ -317,7 +314,7 @@ fock_status batch_tier_times(const fock_shellpairs *const *bases, int nmol, cons
   for (cudaEvent_t x : ev)
     if (x) cudaEventDestroy(x);
   delete bp;
-  if (e != cudaSuccess) return cuda_status(e);
+  if (e != cudaSuccess) return batch_status(e);
   for (size_t i = 0; i < best.size(); ++i) ms_by_tag[i] = best[i];
   return FOCK_OK;
 }
@@ -356,7 +353,7 @@ extern "C" fock_status fock_build_jk_batched(const fock_shellpairs *const *bases
   // the pinned table may still be read by the previous replay
   cudaError_t e = cudaSuccess;
   if (bp->table_pending) e = cudaEventSynchronize(bp->ev_table);
-  if (e != cudaSuccess) return cuda_status(e);
+  if (e != cudaSuccess) return batch_status(e);
   for (int i = 0; i < nmol; ++i) {
     MolEntry m = bp->stat[i];
     m.D = D[i];
@@ -367,7 +364,7 @@ extern "C" fock_status fock_build_jk_batched(const fock_shellpairs *const *bases
   }
   e = cudaEventRecord(bp->ev_in, stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(bp->st, bp->ev_in, 0);
-  if (e != cudaSuccess) return cuda_status(e);
+  if (e != cudaSuccess) return batch_status(e);
   if (!bp->gexec || bp->graph_tau != schwarz_thresh) {
     if (bp->gexec) {
       cudaGraphExecDestroy(bp->gexec);
@@ -384,7 +381,7 @@ extern "C" fock_status fock_build_jk_batched(const fock_shellpairs *const *bases
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
       bp->gexec = nullptr;
-      return cuda_status(e);
+      return batch_status(e);
     }
     bp->graph_tau = schwarz_thresh;
   }
@@ -393,5 +390,5 @@ extern "C" fock_status fock_build_jk_batched(const fock_shellpairs *const *bases
   bp->table_pending = e == cudaSuccess;
   if (e == cudaSuccess) e = cudaEventRecord(bp->ev_out, bp->st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, bp->ev_out, 0);
-  return cuda_status(e);
+  return batch_status(e);
 }

@@ -137,6 +137,7 @@ struct Tier {
   int reg_ck = -1;
   int sb = 0;           // scratch bucket of a full-warp group tier
   int tag = 0;          // class pair + 1 when class pairs are launched apart (tuning)
+  int mixed = 0;        // 1: mixed-precision build (kernel variant with FP32 paths)
   int G;                // lanes per quartet (group kernel)
   int stride;           // scratch doubles per group
   int warps_per_block;
@@ -172,6 +173,12 @@ struct fock_shellpairs {
 };
 
 namespace fk {
+// Status of a CUDA runtime result; a failure also sets the text returned by
+// fock_last_error ("where: error name (description)").  (api.cu)
+fock_status cuda_status(cudaError_t e, const char *where);
+// FOCK_SYNC_CHECK=1 in the environment: synchronise after every launch.
+bool sync_each_launch();
+
 // host helpers (host_pairs.cpp)
 const ClassTables &class_tables();
 const std::vector<double> &boys_table();

@@ -121,6 +121,8 @@ __device__ __forceinline__ float quartet_bound(const KArgs &a, const MolView &mv
 // sorted by G_[ab] (descending), so a skip ends the primitive loop.
 struct PrimScreen {
   float lo, hi;  // FP32 band on G_[ab] G_[cd]
+  float c32;     // mixed precision: primitive quartets of an FP64 quartet with
+                 // G_[ab] G_[cd] below this (cutoff / Dmax) run in FP32 (-1 = none)
   int sA, sB, sC, sD;  // molecule-local shells (FP64 Dmax inside the band)
 };
 
@@ -131,7 +133,8 @@ __device__ __forceinline__ PrimScreen prim_screen(const KArgs &a, const MolView 
   ps.sB = sB - mv.s0;
   ps.sC = sC - mv.s0;
   ps.sD = sD - mv.s0;
-  if (a.tau_eps <= 0.0) {
+  ps.c32 = -1.0f;
+  if (a.tau_eps <= 0.0 && a.fp32_cutoff <= 0.0) {
     ps.lo = ps.hi = -1.0f;
     return ps;
   }
@@ -155,10 +158,24 @@ __device__ __forceinline__ PrimScreen prim_screen(const KArgs &a, const MolView 
     d = fmax(d, Ds[ps.sB * ns + ps.sD]);
     dm = (float)d;
   }
+  if (a.fp32_cutoff > 0.0) ps.c32 = a.fp32_cutoff_f / dm;
+  if (a.tau_eps <= 0.0) {
+    ps.lo = ps.hi = -1.0f;
+    return ps;
+  }
   const float t = a.tau_eps_f / dm;
   ps.lo = t * (1.0f - 1e-4f);
   ps.hi = t * (1.0f + 1e-4f);
   return ps;
+}
+
+// Mixed precision at primitive granularity: inside a quartet whose bound is
+// at least the FP32 cutoff, primitive quartet [ab|cd] is evaluated in FP32
+// when its own bound G_[ab] G_[cd] Dmax is below the cutoff.  Both sides of
+// the split use this one FP32 expression; with each pair's primitives sorted
+// by G_[ab] it is non-increasing along either primitive loop.
+__device__ __forceinline__ bool prim_fp32(const KArgs &a, const PrimScreen &ps, int ip, int jq) {
+  return a.dp.Gpf[ip] * a.dp.Gpf[jq] < ps.c32;
 }
 
 // true = skip primitive quartet (ip | jq)

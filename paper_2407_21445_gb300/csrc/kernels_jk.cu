@@ -149,11 +149,103 @@ __device__ __forceinline__ void boys_seeds_rt_f32(const float *__restrict__ tab,
   }
 }
 
+// Ket transform of one primitive quartet, accumulated over ket primitives:
+// Yh[p][cd] += sum_q (-1)^{|q|} E^{cd}_q R_{p+q}.  Elements are walked in
+// ket-component-major order, so the lanes of a group work on the same ket
+// component (same Hermite box, same trip counts) for consecutive bra
+// Hermite indices; two independent accumulation chains (even / odd v).
+template <int G, class Real>
+__device__ __forceinline__ void ket_transform(const ClassTables &ct, const Real *EQ, const Real *R, Real *Yh,
+                                              int nhab, int ncd, int nd, int lc, int ld, int ck, int gl) {
+  for (int it = gl; it < nhab * ncd; it += G) {
+    const int kc = it / nhab, ph = it - kc * nhab;
+    const int tp = ct.hvec[ph][0], up = ct.hvec[ph][1], vp = ct.hvec[ph][2];
+    const int ic = kc / nd, id = kc - ic * nd;
+    const uint8_t *cc = ct.comp[lc][ic], *dd = ct.comp[ld][id];
+    const int Tx = cc[0] + dd[0], Ty = cc[1] + dd[1], Tz = cc[2] + dd[2];
+    const Real *Eq = EQ + ct.eoff[ck][kc];
+    const int yi = ph * ncd + kc;  // Yh layout: [bra Hermite index][ket component]
+    Real acc0 = Yh[yi], acc1 = Real(0);
+    int e = 0;
+    for (int t = 0; t <= Tx; ++t)
+      for (int u = 0; u <= Ty; ++u) {
+        const int s = (t + u) & 1;  // (-1)^(t+u+v): s for even v, flipped for odd v
+        int v = 0;
+        for (; v < Tz; v += 2, e += 2) {
+          const Real r0 = R[hidx(tp + t, up + u, vp + v)], r1 = R[hidx(tp + t, up + u, vp + v + 1)];
+          acc0 = fma(neg_if(Eq[e], s), r0, acc0);
+          acc1 = fma(neg_if(Eq[e + 1], s ^ 1), r1, acc1);
+        }
+        if (v == Tz) {
+          acc0 = fma(neg_if(Eq[e], s), R[hidx(tp + t, up + u, vp + v)], acc0);
+          ++e;
+        }
+      }
+    Yh[yi] = acc0 + acc1;
+  }
+}
+
+// Bra transform ERI[ab][cd] += sum_p E^{ab}_p Yh[p][cd], computed in Real and
+// added into eri (Acc = Real, or FP64 for the FP32 tail of an FP64 quartet:
+// the FP32 sum converted exactly, then one FP64 add).
+template <int G, class Real, class Acc>
+__device__ __forceinline__ void bra_transform(const ClassTables &ct, const Real *EP, const Real *Yh, Acc *eri, int nab,
+                                              int ncd, int nb, int la, int lb, int cb, int gl) {
+  for (int it = gl; it < nab * ncd; it += G) {
+    const int ka = it / ncd, kc = it - ka * ncd;
+    const int ia = ka / nb, ib = ka - ia * nb;
+    const uint8_t *ac = ct.comp[la][ia], *bc = ct.comp[lb][ib];
+    const int Tx = ac[0] + bc[0], Ty = ac[1] + bc[1], Tz = ac[2] + bc[2];
+    const Real *Ep = EP + ct.eoff[cb][ka];
+    Real acc0, acc1 = Real(0);
+    if constexpr (sizeof(Acc) == sizeof(Real))
+      acc0 = eri[it];
+    else
+      acc0 = Real(0);
+    int e = 0;
+    for (int t = 0; t <= Tx; ++t)
+      for (int u = 0; u <= Ty; ++u) {
+        int v = 0;
+        for (; v < Tz; v += 2, e += 2) {
+          acc0 = fma(Ep[e], Yh[hidx(t, u, v) * ncd + kc], acc0);
+          acc1 = fma(Ep[e + 1], Yh[hidx(t, u, v + 1) * ncd + kc], acc1);
+        }
+        if (v == Tz) {
+          acc0 = fma(Ep[e], Yh[hidx(t, u, v) * ncd + kc], acc0);
+          ++e;
+        }
+      }
+    if constexpr (sizeof(Acc) == sizeof(Real))
+      eri[it] = acc0 + acc1;
+    else
+      eri[it] += f2d_any(acc0 + acc1);
+  }
+}
+
+// FP32 Boys seeds and Hermite integrals of primitive quartet (ip | jq) with
+// pair-relative centres (P - A, Q - C and A - C as FP32 hi/lo parts).
+template <int G>
+__device__ __forceinline__ const float *prim_r_f32(const KArgs &a, const ClassTables &ct, int ip, int jq, float ACx,
+                                                   float ACy, float ACz, int L, float *F, float *R0, float *R1,
+                                                   int gl, unsigned gmask) {
+  const float4 PA = a.dp.paf[ip], QC = a.dp.paf[jq];
+  const float X = PA.x - QC.x + ACx, Y = PA.y - QC.y + ACy, Z = PA.z - QC.z + ACz;
+  const float rs = rsqrtf(PA.w + QC.w);
+  const float alpha = (PA.w * QC.w) * (rs * rs);
+  const float T = alpha * fmaf(X, X, fmaf(Y, Y, Z * Z));
+  boys_seeds_rt_f32<G>(a.boysf, T, rs, -2.0f * alpha, L, F, R0, gl);
+  group_sync(gmask, G);
+  return hermite_r<G, float>(ct, L, X, Y, Z, F, R0, R1, gl, gmask);
+}
+
 // One contracted quartet on a group of G lanes, in FP64 (Real = double) or
 // in FP32 (Real = float, the mixed-precision path below the cutoff: FP32
 // table, pair-relative centres, FP32 copies of U, E and D, exact FP32->FP64
 // conversion of every digested element before the FP64 atomic add).
-template <int G, class Real>
+// TAIL (FP64 part of a mixed build): primitive quartets whose own bound
+// G_[ab] G_[cd] Dmax is below the FP32 cutoff are left out of the FP64 loops
+// and evaluated afterwards in FP32 (prim_fp32), into the same FP64 ERIs.
+template <int G, class Real, bool TAIL = false>
 __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_d, int P, int Q, int gl,
                              unsigned gmask, const MolView &mv) {
   constexpr bool F32 = sizeof(Real) == 4;
@@ -201,10 +293,12 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
   const PrimScreen ps = prim_screen(a, mv, sA, sB, sC, sD);
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
     if (prim_skip(a, mv, ps, ip, pk.x)) break;
+    if (TAIL && prim_fp32(a, ps, ip, pk.x)) break;  // the rest is FP32 work (below)
     const Real *EP = Epool + dp.eoff[ip];
     for (int i = gl; i < nhab * ncd; i += G) Yh[i] = Real(0);
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
       if (prim_skip(a, mv, ps, ip, jq)) break;
+      if (TAIL && prim_fp32(a, ps, ip, jq)) break;
       const Real *EQ = Epool + dp.eoff[jq];
       Real X, Y, Z;
       if constexpr (F32) {
@@ -226,63 +320,43 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
       }
       group_sync(gmask, G);
       const Real *R = hermite_r<G, Real>(ct, L, X, Y, Z, F, R0, R1, gl, gmask);
-      // ket transform, accumulated over ket primitives
-      // elements in ket-component-major order: the lanes of a group then work
-      // on the same ket component (same Hermite box, same trip counts) for
-      // consecutive bra Hermite indices
-      for (int it = gl; it < nhab * ncd; it += G) {
-        const int kc = it / nhab, ph = it - kc * nhab;
-        const int tp = ct.hvec[ph][0], up = ct.hvec[ph][1], vp = ct.hvec[ph][2];
-        const int ic = kc / nd, id = kc - ic * nd;
-        const uint8_t *cc = ct.comp[lc][ic], *dd = ct.comp[ld][id];
-        const int Tx = cc[0] + dd[0], Ty = cc[1] + dd[1], Tz = cc[2] + dd[2];
-        const Real *Eq = EQ + ct.eoff[ck][kc];
-        // two independent accumulation chains (even / odd v) for latency
-        const int yi = ph * ncd + kc;  // Yh layout: [bra Hermite index][ket component]
-        Real acc0 = Yh[yi], acc1 = Real(0);
-        int e = 0;
-        for (int t = 0; t <= Tx; ++t)
-          for (int u = 0; u <= Ty; ++u) {
-            const int s = (t + u) & 1;  // (-1)^(t+u+v): s for even v, flipped for odd v
-            int v = 0;
-            for (; v < Tz; v += 2, e += 2) {
-              const Real r0 = R[hidx(tp + t, up + u, vp + v)], r1 = R[hidx(tp + t, up + u, vp + v + 1)];
-              acc0 = fma(neg_if(Eq[e], s), r0, acc0);
-              acc1 = fma(neg_if(Eq[e + 1], s ^ 1), r1, acc1);
-            }
-            if (v == Tz) {
-              acc0 = fma(neg_if(Eq[e], s), R[hidx(tp + t, up + u, vp + v)], acc0);
-              ++e;
-            }
-          }
-        Yh[yi] = acc0 + acc1;
-      }
+      ket_transform<G, Real>(ct, EQ, R, Yh, nhab, ncd, nd, lc, ld, ck, gl);
       group_sync(gmask, G);
     }
-    // bra transform
-    for (int it = gl; it < nab * ncd; it += G) {
-      const int ka = it / ncd, kc = it - ka * ncd;
-      const int ia = ka / nb, ib = ka - ia * nb;
-      const uint8_t *ac = ct.comp[la][ia], *bc = ct.comp[lb][ib];
-      const int Tx = ac[0] + bc[0], Ty = ac[1] + bc[1], Tz = ac[2] + bc[2];
-      const Real *Ep = EP + ct.eoff[cb][ka];
-      Real acc0 = eri[it], acc1 = Real(0);
-      int e = 0;
-      for (int t = 0; t <= Tx; ++t)
-        for (int u = 0; u <= Ty; ++u) {
-          int v = 0;
-          for (; v < Tz; v += 2, e += 2) {
-            acc0 = fma(Ep[e], Yh[hidx(t, u, v) * ncd + kc], acc0);
-            acc1 = fma(Ep[e + 1], Yh[hidx(t, u, v + 1) * ncd + kc], acc1);
-          }
-          if (v == Tz) {
-            acc0 = fma(Ep[e], Yh[hidx(t, u, v) * ncd + kc], acc0);
-            ++e;
-          }
-        }
-      eri[it] = acc0 + acc1;
-    }
+    bra_transform<G, Real, Real>(ct, EP, Yh, eri, nab, ncd, nb, la, lb, cb, gl);
     group_sync(gmask, G);
+  }
+  if constexpr (TAIL) {
+    if (ps.c32 > 0.0f) {
+      // the FP32 primitive quartets, in the scratch behind the ERIs viewed as
+      // floats (Yh, R0, R1, F need half the room they take in FP64)
+      const float *ha = dp.shl + 6 * sA, *hc = dp.shl + 6 * sC;
+      const float tx = (ha[0] - hc[0]) + (ha[3] - hc[3]);
+      const float ty = (ha[1] - hc[1]) + (ha[4] - hc[4]);
+      const float tz = (ha[2] - hc[2]) + (ha[5] - hc[5]);
+      float *Yf = reinterpret_cast<float *>(Yh);
+      float *R0f = Yf + nhab * ncd;
+      float *R1f = R0f + nhL;
+      float *Ff = R1f + nhL;
+      const int kend = pk.x + pk.y;
+      for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
+        if (prim_skip(a, mv, ps, ip, pk.x)) break;
+        int j0 = pk.x;
+        while (j0 < kend && !prim_fp32(a, ps, ip, j0)) ++j0;
+        if (j0 == kend || prim_skip(a, mv, ps, ip, j0)) continue;
+        for (int i = gl; i < nhab * ncd; i += G) Yf[i] = 0.0f;
+        for (int jq = j0; jq < kend; ++jq) {
+          if (prim_skip(a, mv, ps, ip, jq)) break;
+          group_sync(gmask, G);
+          const float *R = prim_r_f32<G>(a, ct, ip, jq, tx, ty, tz, L, Ff, R0f, R1f, gl, gmask);
+          ket_transform<G, float>(ct, dp.Ef + dp.eoff[jq], R, Yf, nhab, ncd, nd, lc, ld, ck, gl);
+          group_sync(gmask, G);
+        }
+        bra_transform<G, float, double>(ct, dp.Ef + dp.eoff[ip], Yf, reinterpret_cast<double *>(eri), nab, ncd, nb,
+                                        la, lb, cb, gl);
+        group_sync(gmask, G);
+      }
+    }
   }
 
   // digestion into J and K (Sec. 2.3 eight-fold symmetry; J = Jt + Jt^T and
@@ -418,7 +492,7 @@ __global__ void __launch_bounds__(128) k_jk(KArgs a) {
         if constexpr (MODE == 2)
           quartet_body<G, float>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
         else
-          quartet_body<G, double>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
+          quartet_body<G, double, MODE == 1>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
       }
     __syncwarp();
     const int rest = n - k;  // < NG <= 32 entries move to the front
@@ -810,10 +884,7 @@ cudaError_t configure_tier(Tier &t) {
     t.warps_per_block = 4;
     t.smem = 0;
     int per_sm = 0;
-    cudaError_t e = occupancy_reg_a(t.reg_cb, t.reg_ck, 128, &per_sm);
-    if (e == cudaErrorInvalidValue) e = occupancy_reg_b(t.reg_cb, t.reg_ck, 128, &per_sm);
-    if (e == cudaErrorInvalidValue) e = occupancy_reg_c(t.reg_cb, t.reg_ck, 128, &per_sm);
-    if (e == cudaErrorInvalidValue) e = occupancy_reg_d(t.reg_cb, t.reg_ck, 128, &per_sm);
+    cudaError_t e = occupancy_reg(t.reg_cb, t.reg_ck, 128, t.mixed != 0, &per_sm);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -883,11 +954,7 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
     a.Df = Df;
     a.boysf = dev_boys_f();
     set_screen_args(a, tau, Dshf, prim_eps);
-    cudaError_t e = launch_reg_a(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
-    if (e == cudaErrorInvalidValue) e = launch_reg_b(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
-    if (e == cudaErrorInvalidValue) e = launch_reg_c(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
-    if (e == cudaErrorInvalidValue) e = launch_reg_d(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
-    return e;
+    return launch_reg(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
   }
   cudaError_t ae = set_group_smem(t);
   if (ae != cudaSuccess) return ae;
@@ -940,11 +1007,7 @@ cudaError_t launch_jk_tier_batch(const Tier &t, const DevPairs &dp, const MolEnt
   set_screen_args(a, tau, Dshf, prim_eps);
   const int threads = 32 * t.warps_per_block;
   if (t.reg_cb >= 0) {
-    cudaError_t e = launch_reg_a(t.reg_cb, t.reg_ck, a, t.blocks, threads, st);
-    if (e == cudaErrorInvalidValue) e = launch_reg_b(t.reg_cb, t.reg_ck, a, t.blocks, threads, st);
-    if (e == cudaErrorInvalidValue) e = launch_reg_c(t.reg_cb, t.reg_ck, a, t.blocks, threads, st);
-    if (e == cudaErrorInvalidValue) e = launch_reg_d(t.reg_cb, t.reg_ck, a, t.blocks, threads, st);
-    return e;
+    return launch_reg(t.reg_cb, t.reg_ck, a, t.blocks, threads, st);
   }
   cudaError_t ae = set_group_smem(t);
   if (ae != cudaSuccess) return ae;

@@ -112,7 +112,100 @@ __host__ __device__ constexpr int reg_smem_bytes(int threads) {
   return reg_eri_in_smem<LA, LB, LC, LD>() ? ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD) * threads * 8 : 0;
 }
 
+// FP32 primitive quartet [ab|cd] (pair-relative centres, FP32 Boys table and
+// Hermite recursion) added into the half-transformed Y[p][cd].
 template <int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void prim_f32_ket(const KArgs &a, const float4 &PA, int jq, float ACx, float ACy,
+                                             float ACz, float (&Y)[nherm(LA + LB) * ncart(LC) * ncart(LD)]) {
+  constexpr int ND = ncart(LD), NCD = ncart(LC) * ND;
+  constexpr int NHAB = nherm(LA + LB), L = LA + LB + LC + LD, NHL = nherm(L);
+  const DevPairs &dp = a.dp;
+  const float4 QC = dp.paf[jq];
+  const float X = PA.x - QC.x + ACx, Yd = PA.y - QC.y + ACy, Z = PA.z - QC.z + ACz;
+  const float rs = rsqrtf(PA.w + QC.w);
+  const float alpha = (PA.w * QC.w) * (rs * rs);
+  const float T = alpha * fmaf(X, X, fmaf(Yd, Yd, Z * Z));
+  float F[L + 1];
+  boys_seeds_f32<L>(a.boysf, T, rs, -2.0f * alpha, F);
+  float R[NHL];
+  hermite_r_reg<L, float>(F, X, Yd, Z, R);
+  const float *__restrict__ EQ = dp.Ef + dp.eoff[jq];
+  sfor<NCD>([&](auto kci) {
+    constexpr int kc = FK_CI(kci);
+    constexpr TUV c = ct_cart(LC, kc / ND), d = ct_cart(LD, kc % ND);
+    constexpr int TY = c.u + d.u + 1, TZ = c.v + d.v + 1, NQ = (c.t + d.t + 1) * TY * TZ;
+    constexpr int e0 = ct_eoff(LC, LD, kc);
+    sfor<NQ>([&](auto qi) {
+      constexpr int qq = FK_CI(qi);
+      constexpr int t = qq / (TY * TZ), u = (qq / TZ) % TY, v = qq % TZ;
+      const float e1 = __ldg(EQ + e0 + qq);
+      const float ev = ((t + u + v) & 1) ? -e1 : e1;
+      sfor<NHAB>([&](auto pi) {
+        constexpr int p = FK_CI(pi);
+        constexpr TUV h = ct_hvec(p);
+        Y[p * NCD + kc] = fmaf(ev, R[ct_hidx(h.t + t, h.u + u, h.v + v)], Y[p * NCD + kc]);
+      });
+    });
+  });
+}
+
+// FP32 bra transform ERI[ab][cd] += sum_p E^{ab}_p Y[p][cd], each element
+// handed to put(index, value) (accumulation left to the caller).
+template <int LA, int LB, int LC, int LD, class Put>
+__device__ __forceinline__ void bra_f32(const float *__restrict__ EP,
+                                        const float (&Y)[nherm(LA + LB) * ncart(LC) * ncart(LD)], Put &&put) {
+  constexpr int NB = ncart(LB), NAB = ncart(LA) * NB, NCD = ncart(LC) * ncart(LD);
+  sfor<NAB>([&](auto kai) {
+    constexpr int ka = FK_CI(kai);
+    constexpr TUV c = ct_cart(LA, ka / NB), d = ct_cart(LB, ka % NB);
+    constexpr int TY = c.u + d.u + 1, TZ = c.v + d.v + 1, NQ = (c.t + d.t + 1) * TY * TZ;
+    constexpr int e0 = ct_eoff(LA, LB, ka);
+    sfor<NCD>([&](auto kci) {
+      constexpr int kc = FK_CI(kci);
+      float s = 0.0f;
+      sfor<NQ>([&](auto qi) {
+        constexpr int qq = FK_CI(qi);
+        constexpr int t = qq / (TY * TZ), u = (qq / TZ) % TY, v = qq % TZ;
+        s = fmaf(__ldg(EP + e0 + qq), Y[ct_hidx(t, u, v) * NCD + kc], s);
+      });
+      put(ka * NCD + kc, s);
+    });
+  });
+}
+
+// The FP32 part of an FP64 quartet in mixed precision: every primitive quartet
+// that passes the primitive screen but whose bound is below the FP32 cutoff
+// (prim_fp32), i.e. exactly those the FP64 loops of quartet_reg_f64 left out.
+// Per bra primitive the FP32 contributions are summed in FP32 and each
+// element is handed to add(index, value) once.
+template <int LA, int LB, int LC, int LD, class Add>
+__device__ __forceinline__ void prim_tail_f32(const KArgs &a, const MolView &mv, const PrimScreen &ps, int P, int Q,
+                                              int sA, int sC, Add &&add) {
+  constexpr int NCD = ncart(LC) * ncart(LD), NHAB = nherm(LA + LB);
+  const DevPairs &dp = a.dp;
+  const float *ha = dp.shl + 6 * sA, *hc = dp.shl + 6 * sC;
+  const float ACx = (ha[0] - hc[0]) + (ha[3] - hc[3]);
+  const float ACy = (ha[1] - hc[1]) + (ha[4] - hc[4]);
+  const float ACz = (ha[2] - hc[2]) + (ha[5] - hc[5]);
+  const int2 pb = dp.prim[P], pk = dp.prim[Q];
+  const int kend = pk.x + pk.y;
+  for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
+    if (prim_skip(a, mv, ps, ip, pk.x)) break;
+    int j0 = pk.x;
+    while (j0 < kend && !prim_fp32(a, ps, ip, j0)) ++j0;
+    if (j0 == kend || prim_skip(a, mv, ps, ip, j0)) continue;
+    const float4 PA = dp.paf[ip];
+    float Y[NHAB * NCD];
+    sfor<NHAB * NCD>([&](auto i) { Y[FK_CI(i)] = 0.0f; });
+    for (int jq = j0; jq < kend; ++jq) {
+      if (prim_skip(a, mv, ps, ip, jq)) break;
+      prim_f32_ket<LA, LB, LC, LD>(a, PA, jq, ACx, ACy, ACz, Y);
+    }
+    bra_f32<LA, LB, LC, LD>(dp.Ef + dp.eoff[ip], Y, add);
+  }
+}
+
+template <int LA, int LB, int LC, int LD, bool MIXED>
 __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &mv, int P, int Q, int sA, int sB,
                                                 int sC, int sD, double *eri_col) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
@@ -135,12 +228,14 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &m
   const PrimScreen ps = prim_screen(a, mv, sA, sB, sC, sD);
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
     if (prim_skip(a, mv, ps, ip, pk.x)) break;  // weaker bra primitives follow
+    if (MIXED && prim_fp32(a, ps, ip, pk.x)) break;  // the rest is FP32 work (below)
     const PZ P4 = dp.pz[ip];
     const float4 Pf = dp.pf[ip];
     double Y[NHAB * NCD];
     sfor<NHAB * NCD>([&](auto i) { Y[FK_CI(i)] = 0.0; });
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
       if (prim_skip(a, mv, ps, ip, jq)) break;  // weaker ket primitives follow
+      if (MIXED && prim_fp32(a, ps, ip, jq)) break;
       const PrimQuartet q = prim_quartet(P4, Pf, dp.pz[jq], dp.pf[jq]);
       double F[L + 1];
       boys_seeds<L>(a.boys, q, F);
@@ -182,6 +277,13 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &m
           eri_at(ka * NCD + kc) = fma(ev, Y[ct_hidx(t, u, v) * NCD + kc], eri_at(ka * NCD + kc));
         });
       });
+    });
+  }
+
+  // mixed precision: the primitive quartets below the cutoff, in FP32
+  if constexpr (MIXED) {
+    if (ps.c32 > 0.0f) prim_tail_f32<LA, LB, LC, LD>(a, mv, ps, P, Q, sA, sC, [&](int i, float v) {
+      eri_at(i) += f2d_any(v);
     });
   }
 
@@ -371,21 +473,23 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
 // no lane time.  The queues carry over from one unit to the next (all units
 // of a launch are of one class pair), so a warp leaves a partly filled batch
 // only once, after its last unit.
-template <int LA, int LB, int LC, int LD>
+template <int LA, int LB, int LC, int LD, bool MIXED>
 __device__ __forceinline__ void drain_reg(const KArgs &a, const int *qp, const int *qq, int n, bool fp32,
                                           double *eri_col, int lane) {
   if (lane < n) {
     const int P = qp[lane], Q = qq[lane];
     const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
     const MolView mv = mol_view(a, ab.x);
-    if (fp32)
+    if (MIXED && fp32)
       quartet_reg_f32<LA, LB, LC, LD>(a, mv, P, Q, ab.x, ab.y, cd.x, cd.y);
     else
-      quartet_reg_f64<LA, LB, LC, LD>(a, mv, P, Q, ab.x, ab.y, cd.x, cd.y, eri_col);
+      quartet_reg_f64<LA, LB, LC, LD, MIXED>(a, mv, P, Q, ab.x, ab.y, cd.x, cd.y, eri_col);
   }
 }
 
-template <int LA, int LB, int LC, int LD>
+// MIXED = false: FP64 build (no FP32 code in the kernel); true: mixed
+// precision (FP32 quartets below the cutoff, FP32 primitive tails above it).
+template <int LA, int LB, int LC, int LD, bool MIXED>
 __global__ void __launch_bounds__(128) k_reg(KArgs a) {
   extern __shared__ __align__(16) double reg_smem[];
   __shared__ int queues[4][2][2][64];  // per warp: FP64 / FP32 queue of (bra, ket)
@@ -396,7 +500,7 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
   const unsigned lt = (1u << lane) - 1u;
   // drain the first 32 entries of a queue and move the rest (< 32) forward
   auto drain32 = [&](int *qp, int *qq, int &n, bool fp32) {
-    drain_reg<LA, LB, LC, LD>(a, qp, qq, 32, fp32, eri_col, lane);
+    drain_reg<LA, LB, LC, LD, MIXED>(a, qp, qq, 32, fp32, eri_col, lane);
     __syncwarp();
     const bool mv_ = lane + 32 < n;
     const int rp = mv_ ? qp[lane + 32] : 0, rq = mv_ ? qq[lane + 32] : 0;
@@ -423,7 +527,7 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
         const int2 cd = a.dp.ab[Q];
         b = quartet_bound(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
       }
-      const bool is32 = b >= 0.0f && b < a.fp32_cutoff_f, is64 = b >= 0.0f && !is32;
+      const bool is32 = MIXED && b >= 0.0f && b < a.fp32_cutoff_f, is64 = b >= 0.0f && !is32;
       const unsigned m64 = __ballot_sync(0xffffffffu, is64), m32 = __ballot_sync(0xffffffffu, is32);
       if (is64) {
         const int k = n64 + __popc(m64 & lt);
@@ -439,11 +543,13 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
       n32 += __popc(m32);
       __syncwarp();
       if (n64 >= 32) drain32(p64, q64, n64, false);
-      if (n32 >= 32) drain32(p32, q32, n32, true);
+      if constexpr (MIXED) {
+        if (n32 >= 32) drain32(p32, q32, n32, true);
+      }
     }
   }
-  drain_reg<LA, LB, LC, LD>(a, p64, q64, n64, false, eri_col, lane);
-  drain_reg<LA, LB, LC, LD>(a, p32, q32, n32, true, eri_col, lane);
+  drain_reg<LA, LB, LC, LD, MIXED>(a, p64, q64, n64, false, eri_col, lane);
+  if constexpr (MIXED) drain_reg<LA, LB, LC, LD, MIXED>(a, p32, q32, n32, true, eri_col, lane);
 }
 
 // (bra class, ket class) pairs served by register kernels: total L <= 4

@@ -16,8 +16,8 @@ namespace fk {
 cudaError_t launch_reg_a(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st) {
   return reg_launch_impl(cb, ck, a, blocks, threads, st);
 }
-cudaError_t occupancy_reg_a(int cb, int ck, int threads, int *per_sm) {
-  return reg_occupancy_impl(cb, ck, threads, per_sm);
+cudaError_t occupancy_reg_a(int cb, int ck, int threads, bool mixed, int *per_sm) {
+  return reg_occupancy_impl(cb, ck, threads, mixed, per_sm);
 }
 
 }  // namespace fk

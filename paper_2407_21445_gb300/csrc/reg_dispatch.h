@@ -5,11 +5,38 @@
 
 namespace fk {
 cudaError_t launch_reg_a(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st);
-cudaError_t occupancy_reg_a(int cb, int ck, int threads, int *per_sm);
+cudaError_t occupancy_reg_a(int cb, int ck, int threads, bool mixed, int *per_sm);
 cudaError_t launch_reg_b(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st);
-cudaError_t occupancy_reg_b(int cb, int ck, int threads, int *per_sm);
+cudaError_t occupancy_reg_b(int cb, int ck, int threads, bool mixed, int *per_sm);
 cudaError_t launch_reg_c(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st);
-cudaError_t occupancy_reg_c(int cb, int ck, int threads, int *per_sm);
+cudaError_t occupancy_reg_c(int cb, int ck, int threads, bool mixed, int *per_sm);
 cudaError_t launch_reg_d(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st);
-cudaError_t occupancy_reg_d(int cb, int ck, int threads, int *per_sm);
+cudaError_t occupancy_reg_d(int cb, int ck, int threads, bool mixed, int *per_sm);
+cudaError_t launch_reg_e(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st);
+cudaError_t occupancy_reg_e(int cb, int ck, int threads, bool mixed, int *per_sm);
+cudaError_t launch_reg_f(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st);
+cudaError_t occupancy_reg_f(int cb, int ck, int threads, bool mixed, int *per_sm);
+
+// Launch / occupancy of the register kernel of class pair (cb, ck), whichever
+// translation unit instantiates it (cudaErrorInvalidValue if none does).
+inline cudaError_t launch_reg(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st) {
+  cudaError_t (*const fns[])(int, int, const KArgs &, int, int, cudaStream_t) = {
+      launch_reg_a, launch_reg_b, launch_reg_c, launch_reg_d, launch_reg_e, launch_reg_f};
+  cudaError_t e = cudaErrorInvalidValue;
+  for (auto fn : fns) {
+    e = fn(cb, ck, a, blocks, threads, st);
+    if (e != cudaErrorInvalidValue) break;
+  }
+  return e;
+}
+inline cudaError_t occupancy_reg(int cb, int ck, int threads, bool mixed, int *per_sm) {
+  cudaError_t (*const fns[])(int, int, int, bool, int *) = {occupancy_reg_a, occupancy_reg_b, occupancy_reg_c,
+                                                           occupancy_reg_d, occupancy_reg_e, occupancy_reg_f};
+  cudaError_t e = cudaErrorInvalidValue;
+  for (auto fn : fns) {
+    e = fn(cb, ck, threads, mixed, per_sm);
+    if (e != cudaErrorInvalidValue) break;
+  }
+  return e;
+}
 }  // namespace fk

@@ -124,3 +124,33 @@ def test_mixed_kernel_count(env):
     assert fk.fock_kernels_per_build(r64.handle) == fk.fock_kernels_per_build(rmx.handle)
     for x in (n64, nmx, r64, rmx):
         x.close()
+
+
+@pytest.mark.parametrize("group", [0, 1, 8, 32])
+def test_mixed_primitive_tails(env, group):
+    """Inside a quartet whose bound is at or above the cutoff, every primitive
+    quartet whose own bound G_[ab] G_[cd] Dmax is below it runs in FP32 (in the
+    register kernels, group = 0, and in the group kernels forced to 1, 8 and 32
+    lanes per quartet).  A cutoff of 1e-3 sends most primitive quartets of the
+    FP64 quartets of this contracted d/f basis down that path."""
+    rng = np.random.Generator(np.random.PCG64(301))
+    bas = molgen.random_shells(rng, [0, 0, 1, 2, 3, 1, 0, 2], spread=3.0, kmax=6)
+    n = oracle.nbf(bas)
+    D = rng.uniform(-1, 1, (n, n))
+    D = 0.5 * (D + D.T)
+    J, K, st = mixed_jk(env, bas, D, 1e-11, cutoff=1e-3, group_override=group)
+    Jo, Ko = oracle.jk(bas, D, 1e-11)
+    ej, ek, tr = check(J, K, Jo, Ko, D)
+    share_q = st["quartets_fp32"] / st["quartets_evaluated"]
+    share_f = st["flops_model_fp32"] / st["flops_model"]
+    print(f"group {group}: max|dJ|={ej:.2e} max|dK|={ek:.2e} FP32 quartets {share_q:.2f}, FP32 flops {share_f:.2f}")
+
+
+def test_mixed_tails_alkane_stats(env):
+    """C20H42 with the default cutoff: the primitive tails move FP32 work into
+    the FP64 quartets (modelled FP32 flop share above the quartet share)."""
+    p = molgen.problem(1)
+    J, K, st = mixed_jk(env, p.basis, p.D, p.tau)
+    Jo, Ko = oracle.jk(p.basis, p.D, p.tau)
+    check(J, K, Jo, Ko, p.D)
+    assert st["flops_model_fp32"] / st["flops_model"] > st["quartets_fp32"] / st["quartets_evaluated"]

@@ -1,7 +1,10 @@
-"""fock_build_jk_noalloc: the allocation-free variant of fock_build_jk, called
-through the C ABI, must reproduce fock_build_jk on consecutive calls (its
-fixed scratch array keeps the previous call's contents) and refuse bases too
-large for that array.  Collected last on purpose."""
+"""fock_build_jk_noalloc: the allocation-free variant of fock_build_jk, for
+callers that cannot allocate device memory while they run (fixed memory
+budgets, allocator policies without the stream-ordered pool, real-time
+loops).  Called through the C ABI, it must reproduce fock_build_jk on
+consecutive calls (its fixed scratch array keeps the previous call's
+contents), in FP64 and in mixed precision, and refuse bases too large for
+that array.  Collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -11,7 +14,7 @@ import molgen
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-10
+TOL = {0: 1e-10, 1: 1e-7}  # FP64 and mixed-precision tolerances of the parity tests
 
 
 @pytest.fixture(scope="module")
@@ -33,11 +36,11 @@ def _noalloc(L, torch, handle, D, tau, J, K):
                                    ctypes.c_void_p(K.data_ptr()), stream)
 
 
-@pytest.mark.parametrize("config", [0, 1])
-def test_noalloc_matches_fock_build_jk_twice(env, config):
+@pytest.mark.parametrize("config,precision", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_noalloc_matches_fock_build_jk_twice(env, config, precision):
     torch, fk, L = env
     p = molgen.problem(config)
-    b = fk.JKBuilder(p.basis, p.tau)
+    b = fk.JKBuilder(p.basis, p.tau, fk.make_opts(precision=precision))
     D = torch.tensor(p.D, device="cuda", dtype=torch.float64)
     Jr, Kr = b.build(D)
     torch.cuda.synchronize()
@@ -50,7 +53,35 @@ def test_noalloc_matches_fock_build_jk_twice(env, config):
         assert fk.fock_stream_status() == 0
         ej = float(np.abs(J.cpu().numpy() - Jr).max())
         ek = float(np.abs(K.cpu().numpy() - Kr).max())
-        assert ej <= TOL and ek <= TOL, (call, ej, ek)
+        assert ej <= TOL[precision] and ek <= TOL[precision], (call, ej, ek)
+    b.close()
+
+
+def _s_shell_basis(n, seed=11):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return molgen.single_shell_basis([(0, rng.uniform(-40, 40, 3), [0.5], [1.0]) for _ in range(n)])
+
+
+def test_noalloc_size_limit(env):
+    """The fixed array holds 12 nshell^2 bytes plus the counters for FP64
+    handles up to 591 shells; 592 shells are refused without any work."""
+    torch, fk, L = env
+    for n, ok in ((591, True), (592, False)):
+        b = fk.JKBuilder(_s_shell_basis(n), 1e-8)
+        D = torch.eye(n, device="cuda", dtype=torch.float64) * 0.5
+        J = torch.zeros_like(D)
+        K = torch.zeros_like(D)
+        rc = _noalloc(L, torch, b.handle, D, 1e-8, J, K)
+        torch.cuda.synchronize()
+        if ok:
+            assert rc == 0 and fk.fock_stream_status() == 0
+            Jr, Kr = b.build(D)
+            torch.cuda.synchronize()
+            assert float((J - Jr).abs().max()) <= TOL[0] and float((K - Kr).abs().max()) <= TOL[0]
+        else:
+            assert rc == 1  # FOCK_ERR_INVALID_ARG
+            assert float(J.abs().max()) == 0.0 and float(K.abs().max()) == 0.0
+        b.close()
 
 
 def test_noalloc_rejects_basis_beyond_array(env):
