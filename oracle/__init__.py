@@ -24,6 +24,9 @@ _lock = threading.Lock()
 _lib = None
 
 SCREEN_NONE, SCREEN_SCHWARZ, SCREEN_DENSITY = 0, 1, 2
+# density weighting by the blocks that feed J only (D_ab, D_cd) or K only
+# (D_ac, D_ad, D_bc, D_bd): the separate J and K builds (Sec. 4.2, 4.3)
+SCREEN_DENSITY_J, SCREEN_DENSITY_K = 3, 4
 # primitive pair dropped iff G_[ab] * Gmax < tau * EPS_PRUNE; with the density
 # test (SCREEN_DENSITY), primitive quartet skipped iff G_[ab] G_[cd] Dmax < tau * EPS_PRUNE
 EPS_PRUNE = 1e-3
@@ -168,8 +171,9 @@ def schwarz(basis: dict):
 def jk(basis: dict, D: np.ndarray, tau: float = 0.0, mode: int = SCREEN_DENSITY,
        eps_prune: float = EPS_PRUNE, symmetric: bool = True, nthreads: int = 0):
     """J_mn = sum (mn|ls) D_ls, K_mn = sum (ml|ns) D_ls (Eq. fock_build) with
-    the screening `mode` (0 none, 1 Schwarz, 2 Schwarz x six-block density max)
-    and primitive-pair pruning (eps_prune > 0)."""
+    the screening `mode` (0 none, 1 Schwarz, 2 Schwarz x six-block density max,
+    3 / 4 Schwarz x the density max of the blocks feeding J / K -- then only J /
+    only K is the screened build's) and primitive-pair pruning (eps_prune > 0)."""
     args, keep = _basis_args(basis)
     D = np.ascontiguousarray(D, dtype=np.float64)
     n = nbf(basis)

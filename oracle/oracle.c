@@ -580,7 +580,13 @@ static inline void nsum(double *s, double *c, double x) {
   *s = t;
 }
 
-enum { OR_SCREEN_NONE = 0, OR_SCREEN_SCHWARZ = 1, OR_SCREEN_DENSITY = 2 };
+/* Screening modes: none; Schwarz; Schwarz x density max over the six Fock
+ * blocks of the fused J/K build; over the two blocks that feed J (D_ab, D_cd)
+ * or over the four that feed K (D_ac, D_ad, D_bc, D_bd) -- the separate J and
+ * K builds of Sec. 4.2 and 4.3 each weight a quartet by the density elements
+ * it is contracted with. */
+enum { OR_SCREEN_NONE = 0, OR_SCREEN_SCHWARZ = 1, OR_SCREEN_DENSITY = 2, OR_SCREEN_DENSITY_J = 3,
+       OR_SCREEN_DENSITY_K = 4 };
 
 typedef struct {
   or_ctx X;
@@ -630,17 +636,17 @@ static void or_setup_free(or_jk_setup *S) {
   or_ctx_free(&S->X);
 }
 
-/* max |D| over the six shell blocks of (ab|cd) (Sec. 3.2) */
+/* max |D| over the shell blocks of (ab|cd) the screening mode weights with:
+ * all six (Sec. 3.2), the J pair {ab, cd} or the K four {ac, ad, bc, bd} */
 static double or_dmax(const or_jk_setup *S, int a, int b, int c, int d) {
   int ns = S->X.B->nshell;
   const double *Q = S->Dsh;
-  double dm = Q[(size_t)a * ns + b];
-  dm = fmax(dm, Q[(size_t)c * ns + d]);
-  dm = fmax(dm, Q[(size_t)a * ns + c]);
-  dm = fmax(dm, Q[(size_t)a * ns + d]);
-  dm = fmax(dm, Q[(size_t)b * ns + c]);
-  dm = fmax(dm, Q[(size_t)b * ns + d]);
-  return dm;
+  double dj = fmax(Q[(size_t)a * ns + b], Q[(size_t)c * ns + d]);
+  double dk = fmax(fmax(Q[(size_t)a * ns + c], Q[(size_t)a * ns + d]),
+                   fmax(Q[(size_t)b * ns + c], Q[(size_t)b * ns + d]));
+  if (S->mode == OR_SCREEN_DENSITY_J) return dj;
+  if (S->mode == OR_SCREEN_DENSITY_K) return dk;
+  return fmax(dj, dk);
 }
 
 /* The contracted quartet (ab|cd) of a J/K loop: density-weighted primitive
@@ -648,7 +654,7 @@ static double or_dmax(const or_jk_setup *S, int a, int b, int c, int d) {
 static void or_jk_quartet(const or_jk_setup *S, or_work *w, int a, int b, int c, int d, double eps_p,
                           double *eri) {
   int ns = S->X.B->nshell;
-  if (S->mode == OR_SCREEN_DENSITY && eps_p > 0.0)
+  if (S->mode >= OR_SCREEN_DENSITY && eps_p > 0.0)
     or_shell_quartet(&S->X, w, a, b, c, d, -1, -1, S->Gp + ((size_t)a * ns + b) * 64,
                      S->Gp + ((size_t)c * ns + d) * 64, or_dmax(S, a, b, c, d), S->tau * eps_p, eri);
   else
@@ -661,13 +667,7 @@ static int or_screened(const or_jk_setup *S, int a, int b, int c, int d) {
   if (S->mode == OR_SCREEN_NONE) return 0;
   double g = S->G[(size_t)a * ns + b] * S->G[(size_t)c * ns + d];
   if (S->mode == OR_SCREEN_SCHWARZ) return g < S->tau;
-  const double *Q = S->Dsh;
-  double dm = Q[(size_t)a * ns + b];
-  dm = fmax(dm, Q[(size_t)c * ns + d]);
-  dm = fmax(dm, Q[(size_t)a * ns + c]);
-  dm = fmax(dm, Q[(size_t)a * ns + d]);
-  dm = fmax(dm, Q[(size_t)b * ns + c]);
-  dm = fmax(dm, Q[(size_t)b * ns + d]);
+  double dm = or_dmax(S, a, b, c, d);
   /* Sec. 3.2 applies both tests: batches whose Schwarz product is below tau
    * are never launched, and inside the kernel G_ab G_cd Dmax < tau skips. */
   return g < S->tau || g * dm < S->tau;
@@ -675,8 +675,9 @@ static int or_screened(const or_jk_setup *S, int a, int b, int c, int d) {
 
 /*
  * Full J and K.  mode: 0 none, 1 Schwarz (G_ab G_cd < tau), 2 Schwarz x
- * six-block density max.  eps_p > 0 enables primitive-pair pruning and (mode
- * 2) primitive-quartet screening.
+ * six-block density max, 3 / 4 Schwarz x the J / K blocks' density max (only
+ * J / only K is then meaningful).  eps_p > 0 enables primitive-pair pruning
+ * and (modes 2-4) primitive-quartet screening with that mode's density max.
  * symmetric != 0 loops over unique quartets with explicit 8-fold scatter,
  * otherwise over all ordered quartets (N^4 reference used to validate the
  * scatter on small cases).  Returns 0 on success.
