@@ -1,13 +1,17 @@
 """Benchmark of the J/K build (one step = one fock_build_jk call, i.e. one SCF
-iteration's Coulomb + exchange build) on the C20H42 zigzag alkane workload
-(384 Cartesian functions, 6-31G(d)-shaped synthetic basis, FP64, Schwarz
-threshold 1e-10, distance-decaying synthetic density).
+iteration's Coulomb + exchange build).  Default workload: the (H2O)64
+liquid-density water cluster (1,216 Cartesian functions, 6-31G(d)-shaped
+synthetic basis, FP64, Schwarz threshold 1e-10, distance-decaying synthetic
+density), the largest single-GPU configuration.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  `value` is ERIs/s: symmetry-unique contracted
 Cartesian ERIs in quartets passing the Schwarz test, divided by the device
 time of the build, summed over ranks (independent replicas, weak scaling).
+Extra keys: `mixed` (the same workload in mixed precision), `c20h42` (the
+C20H42 alkane in FP64 and mixed precision), `batched` (a batch of TZ-shaped
+molecules up to f through fock_build_jk_batched, FP64 and mixed).
 The reference arm times the CPU oracle (plain FP64 C with OpenMP) on a
 bounded sample of the same workload.
 """
@@ -43,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--carbons", type=int, default=20, help="alkane length for --config 1 (profiling cases)")
     ap.add_argument("--waters", type=int, default=64, help="water molecules for --config 2 (334: 1,002 atoms)")
     ap.add_argument("--nmol", type=int, default=256, help="molecules of the batched workload (--config 3)")
@@ -52,7 +56,16 @@ def parse():
     ap.add_argument("--reg-max-l", type=int, default=0, help="largest total L served by register kernels (0 = default)")
     ap.add_argument("--fp32-cutoff", type=float, default=1e-5, help="mixed leg: FP32 below this quartet bound")
     ap.add_argument("--no-mixed-leg", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true", help="built-in schedule rule instead of the measured one")
+    ap.add_argument("--autotune", action="store_true",
+                    help="measured per-class-pair schedule (fock_autotune) instead of the built-in rule")
+    ap.add_argument("--no-extras", action="store_true", help="skip the c20h42 and batched extra keys")
+    ap.add_argument("--k-thresh", type=float, default=5e-6, help="tau* of the decay-bound exchange mode")
+    ap.add_argument("--batched-nmol", type=int, default=32, help="molecules of the batched extra key")
+    ap.add_argument("--fma-peak", action="store_true",
+                    help="measure the DFMA and FFMA peaks with a register-only FMA probe (built with nvcc) and exit")
+    ap.add_argument("--chain-study", default=None, metavar="N1,N2,...",
+                    help="J-only / K-only build times of zigzag alkanes C_nH_2n+2 for the listed n, exact and "
+                         "decay-bound exchange (one JSON line per n) and exit")
     ap.add_argument("--tune-cache", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                                          "paper_2407_21445_gb300", "_build", "tune_cache.json"))
     ap.add_argument("--tune-nmol", type=int, default=2, help="--config 3: molecules the schedule is measured on")
@@ -66,12 +79,15 @@ def parse():
 
 def workload_config(p, st, precision="fp64"):
     c = p.meta.get("carbons", 20)
-    return {"workload": f"C{c}H{2 * c + 2} zigzag alkane, 6-31G(d)-shaped synthetic basis"
-            if p.meta.get("config") == 1 else p.name, "nbf": int(p.nbf), "nshell": int(len(p.basis["l"])), "schwarz_thresh": p.tau,
-            "screening": "Schwarz + six-block density (Sec. 3.2)",
-            "eris_per_step": int(st["eris_schwarz"]), "quartets_per_step": int(st["quartets_schwarz"]),
-            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",
-            "precision": precision}
+    cfg = {"workload": f"C{c}H{2 * c + 2} zigzag alkane, 6-31G(d)-shaped synthetic basis"
+           if p.meta.get("config") == 1 else p.name, "nbf": int(p.nbf), "nshell": int(len(p.basis["l"])),
+           "schwarz_thresh": p.tau, "screening": "Schwarz + six-block density (Sec. 3.2)",
+           "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",
+           "precision": precision}
+    if st is not None:
+        cfg["eris_per_step"] = int(st["eris_schwarz"])
+        cfg["quartets_per_step"] = int(st["quartets_schwarz"])
+    return cfg
 
 
 class ClockSampler:
@@ -171,14 +187,26 @@ def kernel_hash():
     return h.hexdigest()
 
 
+def oracle_stride(p, seconds):
+    """Stride of oracle.jk_sample (every stride-th outer shell pair) for about
+    `seconds` of CPU work, calibrated on growing samples."""
+    import oracle
+    stride = 1 << 16
+    while True:
+        t0 = time.perf_counter()
+        oracle.jk_sample(p.basis, p.D, p.tau, stride)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 or stride == 1:
+            break
+        stride //= 4
+    return max(1, int(round(stride * dt / seconds)))
+
+
 def cpu_baseline(p, target_s=12.0):
     """The oracle as it stands, on every host core, over a sample of outer shell
     pairs (every stride-th) of the same workload."""
     import oracle
-    t0 = time.perf_counter()
-    n0 = oracle.jk_sample(p.basis, p.D, p.tau, 64)
-    t1 = time.perf_counter() - t0
-    stride = max(1, int(round(64 * t1 / target_s)))
+    stride = oracle_stride(p, target_s)
     t0 = time.perf_counter()
     n = oracle.jk_sample(p.basis, p.D, p.tau, stride)
     dt = time.perf_counter() - t0
@@ -194,11 +222,8 @@ def run_reference(args, rank, world):
         return
     p = molgen.problem(args.config, carbons=args.carbons, waters=args.waters)
     cnt = oracle.count(p.basis, p.D, p.tau)
-    t0 = time.perf_counter()
-    oracle.jk_sample(p.basis, p.D, p.tau, 64)
-    t1 = time.perf_counter() - t0
     budget = 150.0 / max(1, args.steps + args.warmup)  # whole run within a few minutes
-    stride = max(1, int(round(64 * t1 / budget)))
+    stride = oracle_stride(p, budget)
     for _ in range(args.warmup):
         oracle.jk_sample(p.basis, p.D, p.tau, stride)
     tot_n, tot_t = 0.0, 0.0
@@ -249,7 +274,7 @@ def tuned(args, fk, bases, Ds, tau, prec):
     tuning runs before, and outside, every timed region."""
     base = fk.make_opts(precision=prec, fp32_cutoff=args.fp32_cutoff, warp_scratch=args.warp_scratch,
                         reg_max_L=args.reg_max_l)
-    if args.no_autotune:
+    if not args.autotune:
         return base, {"source": "built-in rule"}
     from paper_2407_21445_gb300 import autotune
     o, rec = autotune.tuned_opts(bases, Ds, tau, base, cache=args.tune_cache, reps=3)
@@ -259,107 +284,272 @@ def tuned(args, fk, bases, Ds, tau, prec):
                "class_pairs_changed": len(rec["schedule"])}
 
 
-def run_batched(args, fk, torch, dev, stream, world, rank, dist):
-    """256 molecules of uneven size (TZ-shaped basis up to f) per step through
-    fock_build_jk_batched; FP64 headline plus a mixed-precision leg."""
-    import molgen
-    probs = molgen.batch_problems(args.nmol)
-    tau = probs[0].tau
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+def time_steps(torch, dev, stream, flush, fn, steps, warmup):
+    """`warmup` untimed calls, then `steps` calls each bracketed by CUDA events
+    on the launching stream, with the L2 flushed before each; ms per call."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s_, e_ in evs:
+        flush.zero_()
+        s_.record(stream)
+        fn()
+        e_.record(stream)
+    torch.cuda.synchronize(dev)
+    return [s_.elapsed_time(e_) for s_, e_ in evs]
 
+
+def batched_leg(args, fk, torch, dev, stream, flush, nmol, steps, warmup, e2e_steps=0):
+    """nmol molecules of uneven size (TZ-shaped basis up to f) per step through
+    fock_build_jk_batched, FP64 then mixed precision."""
+    import molgen
+    probs = molgen.batch_problems(nmol)
+    tau = probs[0].tau
+    Ds = [torch.tensor(p.D, device=dev) for p in probs]
+    Js = [torch.empty_like(d) for d in Ds]
+    Ks = [torch.empty_like(d) for d in Ds]
     tunes = {}
 
     def setup(prec):
         k = max(1, min(args.tune_nmol, len(probs)))
         opts, tunes[prec] = tuned(args, fk, [p.basis for p in probs[:k]], Ds[:k], tau, prec)
-        bs = [fk.JKBuilder(p.basis, tau, opts) for p in probs]
-        return bs
+        return [fk.JKBuilder(p.basis, tau, opts) for p in probs]
 
-    def timed(bs, Ds, Js, Ks):
+    def run(bs):
         hs = [b.handle for b in bs]
-        for _ in range(max(3, args.warmup)):
-            fk.fock_build_jk_batched(hs, Ds, tau, Js, Ks)
-        torch.cuda.synchronize(dev)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for s, e in evs:
-            flush.zero_()
-            s.record(stream)
-            fk.fock_build_jk_batched(hs, Ds, tau, Js, Ks)
-            e.record(stream)
-        torch.cuda.synchronize(dev)
-        return float(sum(s.elapsed_time(e) for s, e in evs)) / args.steps
+        return time_steps(torch, dev, stream, flush, lambda: fk.fock_build_jk_batched(hs, Ds, tau, Js, Ks), steps,
+                          warmup)
 
-    Ds = [torch.tensor(p.D, device=dev) for p in probs]
-    Js = [torch.empty_like(d) for d in Ds]
-    Ks = [torch.empty_like(d) for d in Ds]
     bs = setup(fk.FOCK_FP64)
     stats = [b.stats(p.D) for b, p in zip(bs, probs)]
     eris = sum(s["eris_schwarz"] for s in stats)
     flops = sum(s["flops_model"] for s in stats)
+    ms = float(np.mean(run(bs)))
+    st = fk.fock_stream_status()
+    if st != 0:
+        raise SystemExit(f"device status {fk.fock_status_string(st)}")
+    Jref = [j.clone() for j in Js]
+    Kref = [k.clone() for k in Ks]
+    e2e_ms = None
+    nbytes = sum(d.numel() * 8 for d in Ds)
+    if e2e_steps > 0:
+        # pinned host densities in, J and K back to pinned host, every step
+        Dh = [torch.tensor(p.D).pin_memory() for p in probs]
+        Jh = [torch.empty_like(d).pin_memory() for d in Dh]
+        Kh = [torch.empty_like(d).pin_memory() for d in Dh]
+        hs = [b.handle for b in bs]
+        e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e_s.record(stream)
+        for _ in range(e2e_steps):
+            for d, h in zip(Ds, Dh):
+                d.copy_(h, non_blocking=True)
+            fk.fock_build_jk_batched(hs, Ds, tau, Js, Ks)
+            for j, k, jh, kh in zip(Js, Ks, Jh, Kh):
+                jh.copy_(j, non_blocking=True)
+                kh.copy_(k, non_blocking=True)
+        e_e.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e_s.elapsed_time(e_e) / e2e_steps
+    for b in bs:
+        b.close()
+    mbs = setup(fk.FOCK_MIXED)
+    mst = [b.stats(p.D) for b, p in zip(mbs, probs)]
+    mms = float(np.mean(run(mbs)))
+    err = max(max(float((j - jr).abs().max()), float((k - kr).abs().max()))
+              for j, k, jr, kr in zip(Js, Ks, Jref, Kref))
+    for b in mbs:
+        b.close()
+    q32 = sum(s["quartets_fp32"] for s in mst)
+    q = sum(s["quartets_evaluated"] for s in mst)
+    f32 = sum(s["flops_model_fp32"] for s in mst)
+    mflops = sum(s["flops_model"] for s in mst)
+    nbf = [p.nbf for p in probs]
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {
+        "workload": f"{len(probs)} molecules of 5-40 atoms (water clusters, alkanes, mixtures), TZ-shaped "
+                    "synthetic basis up to f, batched build (fock_build_jk_batched, CUDA graph)",
+        "molecules": len(probs), "nbf_total": int(sum(nbf)), "nbf_min": int(min(nbf)), "nbf_max": int(max(nbf)),
+        "schwarz_thresh": tau, "eris_per_step": int(eris), "steps": steps, "warmup": warmup,
+        "fp64": {"ms_per_step": ms, "value": eris / (ms * 1e-3), "unit": UNIT, "achieved_tflops": achieved,
+                 "frac_of_fp64_peak": achieved / FP64_PEAK_TFLOPS, "schedule": tunes.get(fk.FOCK_FP64)},
+        "mixed": {"ms_per_step": mms, "value": eris / (mms * 1e-3), "unit": UNIT, "speedup_vs_fp64": ms / mms,
+                  "fp32_cutoff": args.fp32_cutoff, "max_abs_diff_vs_fp64": err,
+                  "fp32_quartet_share": q32 / max(q, 1.0), "fp32_flop_share": f32 / max(mflops, 1.0),
+                  "schedule": tunes.get(fk.FOCK_MIXED),
+                  "peak_frac": mixed_peak_frac({"flops_model": mflops, "flops_model_fp32": f32}, mms)},
+        "_e2e_ms": e2e_ms, "_nbytes": nbytes, "_eris": eris, "_flops": flops,
+    }
+
+
+def run_batched(args, fk, torch, dev, stream, world, rank, dist):
+    """--config 3: the batched workload as the headline (FP64), mixed as an
+    extra key."""
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     if dist:
         dist.barrier()
     with ClockSampler(dev.index) as clk:
-        ms = timed(bs, Ds, Js, Ks)
-    assert fk.fock_stream_status() == 0
-    Jref = [j.clone() for j in Js]
-    Kref = [k.clone() for k in Ks]
-    # e2e: pinned host densities in, J and K back to pinned host, every step
-    Dh = [torch.tensor(p.D).pin_memory() for p in probs]
-    Jh = [torch.empty_like(d).pin_memory() for d in Dh]
-    Kh = [torch.empty_like(d).pin_memory() for d in Dh]
-    hs = [b.handle for b in bs]
-    e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    e_s.record(stream)
-    for _ in range(args.steps):
-        for d, h in zip(Ds, Dh):
-            d.copy_(h, non_blocking=True)
-        fk.fock_build_jk_batched(hs, Ds, tau, Js, Ks)
-        for j, k, jh, kh in zip(Js, Ks, Jh, Kh):
-            jh.copy_(j, non_blocking=True)
-            kh.copy_(k, non_blocking=True)
-    e_e.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = e_s.elapsed_time(e_e) / args.steps
-    nbytes = sum(d.numel() * 8 for d in Ds)
-    mixed = None
-    if not args.no_mixed_leg:
-        for b in bs:
-            b.close()
-        mbs = setup(fk.FOCK_MIXED)
-        mst = [b.stats(p.D) for b, p in zip(mbs, probs)]
-        mms = timed(mbs, Ds, Js, Ks)
-        err = max(max(float((j - jr).abs().max()), float((k - kr).abs().max()))
-                  for j, k, jr, kr in zip(Js, Ks, Jref, Kref))
-        q32 = sum(s["quartets_fp32"] for s in mst)
-        q = sum(s["quartets_evaluated"] for s in mst)
-        f32 = sum(s["flops_model_fp32"] for s in mst)
-        mixed = {"ms_per_step": mms, "value": eris / (mms * 1e-3), "unit": UNIT, "speedup_vs_fp64": ms / mms,
-                 "fp32_cutoff": args.fp32_cutoff, "max_abs_diff_vs_fp64": err,
-                 "fp32_quartet_share": q32 / max(q, 1.0), "fp32_flop_share": f32 / max(flops, 1.0),
-                 "fp64_flop_frac_of_peak": (flops - f32) / (mms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                 "schedule": tunes.get(fk.FOCK_MIXED),
-                 "peak_frac": mixed_peak_frac({"flops_model": sum(s["flops_model"] for s in mst),
-                                               "flops_model_fp32": f32}, mms)}
+        leg = batched_leg(args, fk, torch, dev, stream, flush, args.nmol, args.steps, max(3, args.warmup),
+                          e2e_steps=args.steps)
+    ms = leg["fp64"]["ms_per_step"]
+    ms = max_over_ranks(ms, dist, dev)
     if rank == 0:
+        eris, nbytes = leg.pop("_eris"), leg.pop("_nbytes")
+        e2e_ms = leg.pop("_e2e_ms")
+        flops = leg.pop("_flops")
         achieved = flops / (ms * 1e-3) / 1e12
-        nbf = [p.nbf for p in probs]
+        cfg = {k: leg[k] for k in ("workload", "molecules", "nbf_total", "nbf_min", "nbf_max", "schwarz_thresh",
+                                   "eris_per_step")}
+        cfg.update({"l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",
+                    "precision": "fp64", "schedule": leg["fp64"]["schedule"]})
         line = {"metric": METRIC, "value": world * eris / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "s_per_iteration": ms * 1e-3,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "s_per_iteration": ms * 1e-3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic",
-                "config": {"workload": f"{len(probs)} molecules of 5-40 atoms (water clusters, alkanes, mixtures), "
-                                       "TZ-shaped synthetic basis up to f, batched build under a CUDA graph",
-                           "molecules": len(probs), "nbf_total": int(sum(nbf)), "nbf_min": int(min(nbf)),
-                           "nbf_max": int(max(nbf)), "schwarz_thresh": tau, "eris_per_step": int(eris),
-                           "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",
-                           "precision": "fp64", "schedule": tunes.get(fk.FOCK_FP64)},
+                "data": "synthetic", "config": cfg,
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None},
                 "e2e": {"value": world * eris / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
                         "d2h_bytes_per_step": int(2 * nbytes)},
-                "mixed": mixed, "clocks": clk.summary()}
+                "mixed": leg["mixed"], "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
+
+
+def alkane_leg(args, fk, torch, dev, stream, flush):
+    """C20H42 (384 functions) in FP64 and in mixed precision, W warm-up and K
+    timed builds each."""
+    import molgen
+    p = molgen.problem(1)
+    D = torch.tensor(p.D, device=dev, dtype=torch.float64)
+    J, K = torch.empty_like(D), torch.empty_like(D)
+    out = {"workload": "C20H42 zigzag alkane, 6-31G(d)-shaped synthetic basis, tau=1e-10", "nbf": int(p.nbf),
+           "steps": args.steps, "warmup": max(3, args.warmup)}
+    ref = None
+    for name, prec in (("fp64", fk.FOCK_FP64), ("mixed", fk.FOCK_MIXED)):
+        b = fk.JKBuilder(p.basis, p.tau, fk.make_opts(precision=prec, fp32_cutoff=args.fp32_cutoff))
+        st = b.stats(p.D)
+        ms = float(np.mean(time_steps(torch, dev, stream, flush, lambda: b.build(D, J, K), args.steps,
+                                      max(3, args.warmup))))
+        leg = {"ms_per_step": ms, "value": st["eris_schwarz"] / (ms * 1e-3), "unit": UNIT}
+        if prec == fk.FOCK_FP64:
+            ach = st["flops_model"] / (ms * 1e-3) / 1e12
+            leg.update(achieved_tflops=ach, frac_of_fp64_peak=ach / FP64_PEAK_TFLOPS)
+            ref = (ms, J.clone(), K.clone())
+        else:
+            leg.update(speedup_vs_fp64=ref[0] / ms,
+                       max_abs_diff_vs_fp64=max(float((J - ref[1]).abs().max()), float((K - ref[2]).abs().max())),
+                       fp32_flop_share=st["flops_model_fp32"] / max(1.0, st["flops_model"]),
+                       peak_frac=mixed_peak_frac(st, ms))
+        out[name] = leg
+        b.close()
+    return out
+
+
+# Register-only FMA probe: every thread runs NCH independent chains
+# x = x * a + b for `iters` iterations and stores their sum (no memory traffic
+# in the loop); 3 warm-up launches, 5 timed with CUDA events.
+FMA_PROBE_SRC = r"""
+#include <cstdio>
+#include <cuda_runtime.h>
+template <class T, int NCH>
+__global__ void k_fma(T *out, int iters, T a, T b) {
+  T x[NCH];
+#pragma unroll
+  for (int i = 0; i < NCH; ++i) x[i] = (T)(threadIdx.x + i);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) x[i] = x[i] * a + b;
+  }
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < NCH; ++i) s += x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+template <class T, int NCH>
+void run(int blocks, int threads, int iters) {
+  T *d = nullptr;
+  if (cudaMalloc(&d, sizeof(T) * blocks * threads) != cudaSuccess) return;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int w = 0; w < 3; ++w) k_fma<T, NCH><<<blocks, threads>>>(d, iters, (T)0.999, (T)0.001);
+  const int reps = 5;
+  cudaEventRecord(e0);
+  for (int r = 0; r < reps; ++r) k_fma<T, NCH><<<blocks, threads>>>(d, iters, (T)0.999, (T)0.001);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaError_t err = cudaGetLastError();
+  cudaFree(d);
+  const double flops = 2.0 * NCH * (double)iters * blocks * threads * reps;
+  printf("{\"pipe\": \"%s\", \"blocks\": %d, \"threads\": %d, \"chains\": %d, \"iters\": %d, "
+         "\"ms_per_launch\": %.4f, \"tflops\": %.4f, \"status\": \"%s\"}\n",
+         sizeof(T) == 8 ? "DFMA" : "FFMA", blocks, threads, NCH, iters, ms / reps, flops / (ms * 1e-3) / 1e12,
+         cudaGetErrorString(err));
+}
+int main() {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  run<double, 8>(sms * 8, 256, 20000);
+  run<double, 8>(sms * 4, 256, 40000);
+  run<double, 16>(sms * 8, 256, 10000);
+  run<float, 8>(sms * 8, 256, 400000);
+  run<float, 16>(sms * 8, 256, 200000);
+  run<float, 8>(sms * 16, 256, 200000);
+  return 0;
+}
+"""
+
+
+def fma_peak():
+    """Build and run the FMA probe (sm_103a) with nvidia-smi clocks sampled."""
+    import shutil
+    out_dir = os.path.join(ROOT, "paper_2407_21445_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    src, exe = os.path.join(out_dir, "fma_probe.cu"), os.path.join(out_dir, "fma_probe")
+    with open(src, "w") as f:
+        f.write(FMA_PROBE_SRC)
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+    with ClockSampler(0) as clk:
+        r = subprocess.run([exe], capture_output=True, text=True, check=True)
+    for line in r.stdout.splitlines():
+        print(line)
+    print(json.dumps({"clocks": clk.summary()}))
+
+
+def chain_study(args, fk, torch, dev, stream):
+    """Sec. 6.4.1-style scaling study: per alkane length, the device time of a
+    J-only build, a K-only build with the exact exchange test and a K-only
+    build with the decay-bound test (tau* = --k-thresh), and the decay mode's
+    K error against the exact one."""
+    import molgen
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for n in [int(x) for x in args.chain_study.split(",")]:
+        p = molgen.problem(1, carbons=n)
+        D = torch.tensor(p.D, device=dev, dtype=torch.float64)
+        ex = fk.JKBuilder(p.basis, p.tau)
+        dc = fk.JKBuilder(p.basis, p.tau, fk.make_opts(k_mode=1, k_thresh=args.k_thresh))
+        out = {"carbons": n, "nbf": int(p.nbf), "nshell": int(len(p.basis["l"])), "schwarz_thresh": p.tau,
+               "k_thresh": args.k_thresh}
+        res = {}
+        for name, b, parts in (("j", ex, "j"), ("k_exact", ex, "k"), ("k_decay", dc, "k"), ("jk_exact", ex, "jk")):
+            ms = time_steps(torch, dev, stream, flush, lambda: b.build(D, parts=parts), args.steps,
+                            max(1, args.warmup))
+            out[name + "_ms"] = float(np.mean(ms))
+            res[name] = b.build(D, parts=parts)
+        torch.cuda.synchronize(dev)
+        dK = res["k_decay"][1] - res["k_exact"][1]
+        out["k_decay_max_abs_err"] = float(dK.abs().max())
+        out["k_decay_tr_D_err"] = abs(float((D * dK).sum()))
+        H, L, R, _ = dc.decay_bound(D)
+        out.update(H=H, Lambda=L, R_mean=float(np.mean(R)))
+        st = ex.stats(p.D)
+        out["eris_schwarz"] = int(st["eris_schwarz"])
+        ex.close()
+        dc.close()
+        print(json.dumps(out), flush=True)
 
 
 def main():
@@ -375,6 +565,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.fma_peak:
+        return fma_peak()
 
     import torch
 
@@ -389,6 +581,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
+    if args.chain_study:
+        return chain_study(args, fk, torch, dev, stream)
     if args.config == 3:
         return run_batched(args, fk, torch, dev, stream, world, rank, dist)
     p = molgen.problem(args.config, carbons=args.carbons, waters=args.waters)
@@ -434,11 +628,12 @@ def main():
     Jh = torch.empty_like(Dh).pin_memory()
     Kh = torch.empty_like(Dh).pin_memory()
     e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = min(args.steps, 3)  # seconds-long builds: the copies are a small share already
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     e_s.record(stream)
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         D.copy_(Dh, non_blocking=True)
         builder.build(D, J, K)
         Jh.copy_(J, non_blocking=True)
@@ -447,7 +642,7 @@ def main():
     torch.cuda.synchronize(dev)
     e2e_ms = e_s.elapsed_time(e_e)
     e2e_ms = max_over_ranks(e2e_ms, dist, dev)
-    e2e_value = world * st["eris_schwarz"] * args.steps / (e2e_ms * 1e-3)
+    e2e_value = world * st["eris_schwarz"] * e2e_steps / (e2e_ms * 1e-3)
     assert np.isfinite(Jh.numpy()).all() and np.isfinite(Kh.numpy()).all()
 
     # ---- mixed-precision leg on the same workload (extra key) --------------
@@ -459,17 +654,8 @@ def main():
         builder.build(D, J, K)
         Jm = torch.empty_like(D)
         Km = torch.empty_like(D)
-        for _ in range(max(3, args.warmup)):
-            mb.build(D, Jm, Km)
-        torch.cuda.synchronize(dev)
-        mevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for s, e in mevs:
-            flush.zero_()
-            s.record(stream)
-            mb.build(D, Jm, Km)
-            e.record(stream)
-        torch.cuda.synchronize(dev)
-        mms = float(sum(s.elapsed_time(e) for s, e in mevs)) / args.steps
+        msteps = min(args.steps, 5)
+        mms = float(np.mean(time_steps(torch, dev, stream, flush, lambda: mb.build(D, Jm, Km), msteps, 3)))
         err = max(float((Jm - J).abs().max()), float((Km - K).abs().max()))
         trd = abs(float((D * (2 * Jm - Km)).sum() - (D * (2 * J - K)).sum()))
         mixed = {"ms_per_step": mms, "value": st["eris_schwarz"] / (mms * 1e-3), "unit": UNIT,
@@ -477,8 +663,15 @@ def main():
                  "max_abs_diff_vs_fp64": err, "trace_diff_vs_fp64": trd,
                  "fp32_quartet_share": mst["quartets_fp32"] / max(1.0, mst["quartets_evaluated"]),
                  "fp32_flop_share": mst["flops_model_fp32"] / max(1.0, mst["flops_model"]), "schedule": mtune,
-                 "peak_frac": mixed_peak_frac(mst, mms)}
+                 "peak_frac": mixed_peak_frac(mst, mms), "steps": msteps, "warmup": 3}
         mb.close()
+
+    # ---- extra keys: C20H42 (FP64 and mixed) and a TZ batch up to f ---------
+    extras = {}
+    if not args.no_extras and args.config == 2 and world == 1:
+        extras["c20h42"] = alkane_leg(args, fk, torch, dev, stream, flush)
+        bl = batched_leg(args, fk, torch, dev, stream, flush, args.batched_nmol, 1, 1)
+        extras["batched"] = {k: v for k, v in bl.items() if not k.startswith("_")}
 
     if rank == 0:
         achieved = st["flops_model"] / (ms * 1e-3) / 1e12
@@ -493,13 +686,14 @@ def main():
                          "peak_note": "FP64 pipe, derived 152 SMs x 2 FMA/clk x 2.07 GHz; achieved = modelled "
                                       "FP64 flops of evaluated quartets / device time of the whole build"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(D.numel() * 8),
-                    "d2h_bytes_per_step": int(2 * D.numel() * 8)},
+                    "d2h_bytes_per_step": int(2 * D.numel() * 8), "steps": e2e_steps},
             "gpu_launches": int(nk * args.steps),
             "mixed": mixed,
             "clocks": clk.summary(),
             "work": {k: st[k] for k in ("quartets_evaluated", "eris_evaluated", "prim_quartets",
                                         "flops_model", "prim_pairs", "pairs")},
         }
+        line.update(extras)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p)
         print(json.dumps(line), flush=True)

@@ -55,6 +55,13 @@ typedef enum {
 
 enum { FOCK_FP64 = 0, FOCK_MIXED = 1 };
 
+/* Exchange screening modes (fock_opts.k_mode). */
+enum {
+  FOCK_K_EXACT = 0,       /* rigorous density-weighted Schwarz test (Sec. 3.2)     */
+  FOCK_K_DECAY_BOUND = 1  /* heuristic decay bound of Sec. 4.3.1: K contributions
+                             below k_thresh by H exp(-Lambda r) are not evaluated */
+};
+
 /* Basis description: host pointers, caller-owned, read only during
  * fock_shellpairs_build.  Shell s has angular momentum l[s] (0..3), nprim[s]
  * (1..8) primitives whose exponents and raw contraction coefficients (for
@@ -109,7 +116,16 @@ typedef struct {
                              kernel with that many lanes per quartet (raised
                              where a warp's scratch would not fit).  Filled by
                              fock_autotune.  Ignored where group_override > 0. */
-  int8_t reserved[4];
+  int32_t k_mode;         /* FOCK_K_EXACT (default) or FOCK_K_DECAY_BOUND: the
+                             exchange part of a quartet is needed when, for one
+                             of its four K blocks (x, y), G_ab G_cd
+                             H exp(-Lambda max(0, |XY| - R_x - R_y)) >= k_thresh
+                             (Sec. 4.3.1: |D| <= H exp(-Lambda r) fitted to the
+                             density on every call; R_s the largest distance
+                             from shell s to a shell it forms a kept pair with);
+                             the Coulomb part keeps the exact test            */
+  double k_thresh;        /* tau* of the decay-bound mode (> 0; 5e-6 in the
+                             paper's experiments); ignored in FOCK_K_EXACT     */
 } fock_opts;
 
 /* sizeof(fock_opts) as compiled into the library (binding layout check). */
@@ -160,13 +176,19 @@ FOCK_API int32_t fock_nbasis(const fock_shellpairs *sp);
  * quartet whose own bound G_[ab] G_[cd] Dmax is below fp32_cutoff is
  * evaluated in FP32; all contributions are accumulated in FP64.
  *   D: device, N x N row-major float64, symmetric (read).
- *   J, K: device, N x N row-major float64 (overwritten).
+ *   J, K: device, N x N row-major float64 (overwritten).  One of them may be
+ *   NULL: then only the other is built, and the density test of a quartet
+ *   uses only the blocks that feed it (J: D_ab, D_cd; K: D_ac, D_ad, D_bc,
+ *   D_bd), as the paper's separate J and K schemes do (Sec. 4.2, 4.3).
  *   schwarz_thresh >= the value the handle was built with.
  *   stream: all work is enqueued on it; no host synchronisation.
  * Per-call scratch (shell-block density maxima, work counters) is taken from
  * the stream-ordered allocator (cudaMallocAsync) and released on the stream.
- * Errors (synchronous): FOCK_ERR_INVALID_ARG (null pointers, threshold below
- * the build threshold), FOCK_ERR_OOM, FOCK_ERR_CUDA.  A NaN/Inf in D sets
+ * With k_mode FOCK_K_DECAY_BOUND the handle's exchange test is the
+ * heuristic decay bound (see fock_opts; H and Lambda are fitted on the device
+ * from the shell-block maxima of D on every call).
+ * Errors (synchronous): FOCK_ERR_INVALID_ARG (null pointers, J and K both
+ * NULL, threshold below the build threshold), FOCK_ERR_OOM, FOCK_ERR_CUDA.  A NaN/Inf in D sets
  * FOCK_ERR_NONFINITE in the status word (fock_stream_status).  With the
  * environment variable FOCK_SYNC_CHECK=1 every launch is followed by a
  * stream synchronisation so that a failure names its kernel
@@ -174,6 +196,25 @@ FOCK_API int32_t fock_nbasis(const fock_shellpairs *sp);
  */
 FOCK_API fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, double schwarz_thresh,
                           double *J, double *K, cudaStream_t stream);
+
+/*
+ * The density decay bound of Sec. 4.3.1 (Eq. density_bound, |D_cd| <=
+ * H exp(-Lambda |CD|)) as fock_build_jk fits it in FOCK_K_DECAY_BOUND mode:
+ * the shell-block maxima max|D| of every pair of shells on different atoms
+ * (atom from fock_basis_desc.atom, or one atom per shell when NULL) are
+ * binned by the distance of the shell centres in bins of 0.5 bohr; ln of each
+ * bin's maximum is fitted by least squares to ln H - Lambda r (r the bin
+ * centre), and ln H is then raised until the line lies above every bin's
+ * maximum over the whole bin, so that the bound holds for every such element.
+ * Also the per-shell radius R_s (largest centre distance from shell s to a
+ * shell it forms a kept pair with, Sec. 4.3.1 read with the condition
+ * G >= tau) and G_s (largest Schwarz factor of those pairs).
+ *   D: device, N x N row-major float64.  out_HL[0] = H, out_HL[1] = Lambda
+ *   (bohr^-1); R, G: host arrays of nshell doubles (either may be NULL).
+ * Synchronises the stream.  Errors: FOCK_ERR_INVALID_ARG, FOCK_ERR_CUDA.
+ */
+FOCK_API fock_status fock_decay_bound(const fock_shellpairs *sp, const double *D, double out_HL[2], double *R,
+                                      double *G, cudaStream_t stream);
 
 /*
  * fock_build_jk without any device allocation.  The paper has no counterpart:
@@ -186,9 +227,12 @@ FOCK_API fock_status fock_build_jk(const fock_shellpairs *sp, const double *D, d
  * scratch lives in a fixed 4 MiB array inside the library, which every GPU
  * that loads the library keeps until the process exits.  A call needs
  * 12 nshell^2 bytes (shell-block density maxima in FP64 and FP32), plus
- * 4 N^2 bytes with FOCK_MIXED (the FP32 copy of D), plus a few hundred bytes
- * of work counters: FP64 handles fit up to 591 shells.  Handles that do not
- * fit return FOCK_ERR_INVALID_ARG without doing any work.  Every call looks
+ * 4 N^2 bytes with FOCK_MIXED (the FP32 copy of D), plus 12 nshell^2 bytes
+ * and 8 bytes per 0.5 bohr of the molecule's extent with FOCK_K_DECAY_BOUND
+ * (the bounds and the GDG products), plus a few hundred bytes of work
+ * counters: FP64 handles in the exact exchange mode fit up to 591 shells.
+ * Handles that do not fit return FOCK_ERR_INVALID_ARG without doing any work.
+ * J or K may be NULL as in fock_build_jk.  Every call looks
  * up the array's device address (cudaGetSymbolAddress); the first call on
  * each device also loads the library's device code there, so make that first
  * call before any stream capture.  Every call uses the same array: calls

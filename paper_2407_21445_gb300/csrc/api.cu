@@ -70,11 +70,13 @@ void class_l(int c, int &la, int &lb) {
 // Taylor, seeds, R recursion, ket transform) and per bra primitive (bra
 // transform).  Per primitive quartet: zeta + eta 1, 1/sqrt by one Newton-
 // Householder step 8, alpha 3, -2 alpha 1, P - Q 3, T 6, T_i - T 1 = 23;
-// per Boys order 7 Horner FMAs 14, seed scaling 1, power of -2 alpha 1 = 16.
+// per Boys order 4 FP64 Horner FMAs 8 (the four highest Taylor terms run on
+// the FP32 units and are not counted), seed scaling 1, power of -2 alpha 1
+// = 10.
 double flops_prim(int Lab, int L, int ck) {
   const ClassTables &ct = class_tables();
   double f = 23.0;                  // alpha, T, 1/sqrt(zeta + eta)
-  f += (L + 1) * 16.0;              // Taylor Horner + seed scaling
+  f += (L + 1) * 10.0;              // Taylor Horner + seed scaling
   for (int n = L - 1; n >= 0; --n)  // Hermite recursion
     for (int e = 1; e < nherm(L - n); ++e) {
       const int t = ct.hvec[e][0], u = ct.hvec[e][1], w = ct.hvec[e][2];
@@ -176,6 +178,9 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   const size_t o_Uf = pk.add(st.Uf.data(), st.Uf.size() * sizeof(float));
   const size_t o_Ef = pk.add(st.Ef.data(), st.Ef.size() * sizeof(float));
   const size_t o_smol = pk.add(st.smol.data(), st.smol.size() * sizeof(int));
+  const size_t o_satom = pk.add(st.satom.data(), st.satom.size() * sizeof(int));
+  const size_t o_sRG = pk.add(st.sRG.data(), st.sRG.size() * sizeof(float2));
+  const size_t o_Gn = pk.add(st.Gn.data(), st.Gn.size() * sizeof(float));
   const size_t o_units = pk.add(units.data(), units.size() * sizeof(Unit));
   const size_t total = (pk.off + 255) & ~(size_t)255;
   char *d = nullptr;
@@ -206,6 +211,9 @@ fock_status upload(const Staging &st, const std::vector<Unit> &units, void **bas
   dp.paf = (const float4 *)(d + o_paf);
   dp.Gf = (const float *)(d + o_Gf);
   dp.smol = st.smol.empty() ? nullptr : (const int *)(d + o_smol);
+  dp.satom = st.satom.empty() ? nullptr : (const int *)(d + o_satom);
+  dp.sRG = st.sRG.empty() ? nullptr : (const float2 *)(d + o_sRG);
+  dp.Gn = st.Gn.empty() ? nullptr : (const float *)(d + o_Gn);
   dp.shl = (const float *)(d + o_shl);
   dp.Uf = (const float *)(d + o_Uf);
   dp.Ef = (const float *)(d + o_Ef);
@@ -304,6 +312,8 @@ fock_opts default_opts() {
   o.precision = FOCK_FP64;
   o.fp32_cutoff = 1e-5;
   o.prune_eps = 1e-3;
+  o.k_mode = FOCK_K_EXACT;
+  o.k_thresh = 5e-6;
   return o;
 }
 
@@ -313,6 +323,8 @@ bool valid_opts(const fock_opts &o) {
       (o.group_override & (o.group_override - 1)) != 0)
     return false;
   if (o.tune_isolate != 0 && o.tune_isolate != 1) return false;
+  if (o.k_mode != FOCK_K_EXACT && o.k_mode != FOCK_K_DECAY_BOUND) return false;
+  if (o.k_mode == FOCK_K_DECAY_BOUND && !(o.k_thresh > 0.0 && isfinite(o.k_thresh))) return false;
   for (int i = 0; i < FOCK_NCLASS * FOCK_NCLASS; ++i) {
     const int v = o.schedule[i];
     if (!(v == -1 || v == 0 || v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32)) return false;
@@ -475,6 +487,61 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     return x.G > y.G;
   });
   const int npair = (int)keep.size();
+  // ---- decay-bound radii (Sec. 4.3.1): R_s the largest centre distance from
+  // shell s to a shell it forms a kept pair with (the paper's condition on
+  // G_[ac] read as "significant"), G_s the largest Schwarz factor of those
+  // pairs; atoms from the description, else shells sharing a centre -------
+  {
+    sp->h_R.assign(ns, 0.0);
+    sp->h_Gs.assign(ns, 0.0);
+    for (const PairRec &r : keep) {
+      const int a = all.ab[r.idx].x, b = all.ab[r.idx].y;
+      double d2 = 0.0;
+      for (int x = 0; x < 3; ++x) {
+        const double t = desc->center[3 * a + x] - desc->center[3 * b + x];
+        d2 += t * t;
+      }
+      const double d = sqrt(d2);
+      sp->h_R[a] = std::max(sp->h_R[a], d);
+      sp->h_R[b] = std::max(sp->h_R[b], d);
+      sp->h_Gs[a] = std::max(sp->h_Gs[a], r.G);
+      sp->h_Gs[b] = std::max(sp->h_Gs[b], r.G);
+    }
+    st.satom.resize(ns);
+    for (int s = 0; s < ns; ++s) {
+      if (desc->atom) {
+        st.satom[s] = desc->atom[s];
+        continue;
+      }
+      st.satom[s] = s;
+      for (int t = 0; t < s; ++t)
+        if (desc->center[3 * t] == desc->center[3 * s] && desc->center[3 * t + 1] == desc->center[3 * s + 1] &&
+            desc->center[3 * t + 2] == desc->center[3 * s + 2]) {
+          st.satom[s] = st.satom[t];
+          break;
+        }
+    }
+    if (o.k_mode == FOCK_K_DECAY_BOUND) {  // GDG factors n_z G_xz of kept pairs (both orders)
+      st.Gn.assign((size_t)ns * ns, 0.0f);
+      for (const PairRec &r : keep) {
+        const int a = all.ab[r.idx].x, b = all.ab[r.idx].y;
+        st.Gn[(size_t)a * ns + b] = (float)(r.G * ncart(desc->l[b]));
+        st.Gn[(size_t)b * ns + a] = (float)(r.G * ncart(desc->l[a]));
+      }
+    }
+    st.sRG.resize(ns);
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int s = 0; s < ns; ++s) {
+      st.sRG[s] = make_float2((float)sp->h_R[s], (float)sp->h_Gs[s]);
+      for (int x = 0; x < 3; ++x) {
+        lo[x] = std::min(lo[x], desc->center[3 * s + x]);
+        hi[x] = std::max(hi[x], desc->center[3 * s + x]);
+      }
+    }
+    double diag2 = 0.0;
+    for (int x = 0; x < 3; ++x) diag2 += (hi[x] - lo[x]) * (hi[x] - lo[x]);
+    sp->decay_nbins = (int)floor(sqrt(diag2) / 0.5) + 2;
+  }
   for (const PairRec &r : keep) {
     const int P = r.idx;
     st.ab.push_back(all.ab[P]);
@@ -678,36 +745,66 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
 
 extern "C++" {
 namespace fk {
+ScratchLayout scratch_layout(const fock_shellpairs *sp) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t ns = sp->nshell, n = sp->nbf, nt = sp->tiers.size();
+  const bool mixed = sp->opts.precision == FOCK_MIXED && sp->opts.fp32_cutoff > 0.0;
+  const bool decay = sp->opts.k_mode == FOCK_K_DECAY_BOUND;
+  ScratchLayout L;
+  L.cnt_off = al(sizeof(double) * ns * ns);
+  L.df_off = al(L.cnt_off + sizeof(int) * (2 * nt + 1));
+  L.dshf_off = mixed ? al(L.df_off + sizeof(float) * n * n) : L.df_off;
+  L.total = L.dshf_off + sizeof(float) * ns * ns;
+  if (decay) {
+    L.w_off = al(L.total);
+    L.bins_off = al(L.w_off + sizeof(float) * ns * ns);
+    L.hl_off = al(L.bins_off + sizeof(double) * sp->decay_nbins);
+    L.t_off = al(L.hl_off + 2 * sizeof(double));
+    L.gdg_off = al(L.t_off + sizeof(float) * ns * ns);
+    L.total = L.gdg_off + sizeof(float) * ns * ns;
+  }
+  return L;
+}
+
 // fock_build_jk with, when ev is given (tiers + 1 events), an event recorded
 // before every tier launch and one after the last.
 fock_status build_jk_events(const fock_shellpairs *sp, const double *D, double schwarz_thresh, double *J,
                             double *K, cudaStream_t stream, const cudaEvent_t *ev) {
-  if (!sp || !D || !J || !K) return FOCK_ERR_INVALID_ARG;
+  if (!sp || !D || (!J && !K)) return FOCK_ERR_INVALID_ARG;
   if (!(schwarz_thresh >= sp->tau_build) || !isfinite(schwarz_thresh)) return FOCK_ERR_INVALID_ARG;
   const int ns = sp->nshell, n = sp->nbf;
   const size_t nt = sp->tiers.size();
   const bool mixed = sp->opts.precision == FOCK_MIXED && sp->opts.fp32_cutoff > 0.0;
-  const size_t dsh_bytes = sizeof(double) * (size_t)ns * ns;
-  const size_t cnt_off = (dsh_bytes + 255) & ~(size_t)255;
-  const size_t df_off = (cnt_off + sizeof(int) * (2 * nt + 1) + 255) & ~(size_t)255;
-  const size_t dshf_off = mixed ? (df_off + sizeof(float) * (size_t)n * n + 255) & ~(size_t)255 : df_off;
-  const size_t total = dshf_off + sizeof(float) * (size_t)ns * ns;
+  const ScratchLayout L = scratch_layout(sp);
   char *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&scratch, total, stream);
+  cudaError_t e = cudaMallocAsync((void **)&scratch, L.total, stream);
   if (e != cudaSuccess) return to_status(e);
   double *Dsh = (double *)scratch;
-  int *counters = (int *)(scratch + cnt_off);
-  float *Df = mixed ? (float *)(scratch + df_off) : nullptr;
-  float *Dshf = (float *)(scratch + dshf_off);
+  int *counters = (int *)(scratch + L.cnt_off);
+  float *Df = mixed ? (float *)(scratch + L.df_off) : nullptr;
+  float *Dshf = (float *)(scratch + L.dshf_off);
+  CallParts cp;
+  cp.parts = (J ? 1 : 0) | (K ? 2 : 0);
+  const bool decay = sp->opts.k_mode == FOCK_K_DECAY_BOUND && K;
   const bool chk = sync_check();
   const char *where = "memset";
   e = cudaMemsetAsync(counters, 0, sizeof(int) * (2 * nt + 1), stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(J, 0, sizeof(double) * (size_t)n * n, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(K, 0, sizeof(double) * (size_t)n * n, stream);
+  if (e == cudaSuccess && J) e = cudaMemsetAsync(J, 0, sizeof(double) * (size_t)n * n, stream);
+  if (e == cudaSuccess && K) e = cudaMemsetAsync(K, 0, sizeof(double) * (size_t)n * n, stream);
   if (e == cudaSuccess) {
     where = "k_dprep";
     e = launch_dprep(D, n, sp->dev.sbf, sp->dev.sl, ns, Dsh, stream, Df, Dshf);
     if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
+  }
+  if (e == cudaSuccess && decay) {
+    where = "decay bound";
+    float *W = (float *)(scratch + L.w_off);
+    e = launch_decay_bound(sp->dev, Dsh, sp->decay_nbins, (double *)(scratch + L.bins_off),
+                           (double *)(scratch + L.hl_off), W, stream, sp->dev.Gn, Dshf,
+                           (float *)(scratch + L.t_off), (float *)(scratch + L.gdg_off), sp->opts.k_thresh);
+    if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
+    cp.Wsh = W;
+    cp.k_thresh = sp->opts.k_thresh;
   }
   static char tier_name[64];
   for (size_t t = 0; t < nt && e == cudaSuccess; ++t) {
@@ -716,7 +813,7 @@ fock_status build_jk_events(const fock_shellpairs *sp, const double *D, double s
     if (ev) e = cudaEventRecord(ev[t], stream);
     if (e == cudaSuccess)
       e = launch_jk_tier(sp->tiers[t], sp->dev, D, Dsh, schwarz_thresh, sp->prune_eps, J, K, counters + t,
-                         counters + nt + t, stream, Df, sp->opts.fp32_cutoff, Dshf);
+                         counters + nt + t, stream, Df, sp->opts.fp32_cutoff, Dshf, cp);
     if (e == cudaSuccess && chk) e = cudaStreamSynchronize(stream);
   }
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[nt], stream);
@@ -745,6 +842,37 @@ fock_status fock_stream_status(cudaStream_t stream) {
   int rc = read_and_clear_status(stream, &v);
   if (rc) return FOCK_ERR_CUDA;
   return (fock_status)v;
+}
+
+fock_status fock_decay_bound(const fock_shellpairs *sp, const double *D, double out_HL[2], double *R, double *G,
+                             cudaStream_t stream) {
+  if (!sp || !D || !out_HL) return FOCK_ERR_INVALID_ARG;
+  const int ns = sp->nshell;
+  const size_t bins_off = (sizeof(double) * (size_t)ns * ns + 255) & ~(size_t)255;
+  const size_t hl_off = (bins_off + sizeof(double) * sp->decay_nbins + 255) & ~(size_t)255;
+  char *scratch = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&scratch, hl_off + 2 * sizeof(double), stream);
+  if (e != cudaSuccess) return to_status(e, "cudaMallocAsync");
+  const char *where = "k_dprep";
+  e = launch_dprep(D, sp->nbf, sp->dev.sbf, sp->dev.sl, ns, (double *)scratch, stream);
+  if (e == cudaSuccess) {
+    where = "decay bound";
+    e = launch_decay_bound(sp->dev, (double *)scratch, sp->decay_nbins, (double *)(scratch + bins_off),
+                           (double *)(scratch + hl_off), nullptr, stream);
+  }
+  if (e == cudaSuccess) {
+    where = "copy";
+    e = cudaMemcpyAsync(out_HL, scratch + hl_off, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream);
+  }
+  cudaError_t e2 = cudaFreeAsync(scratch, stream);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return to_status(e, where);
+  for (int s = 0; s < ns; ++s) {
+    if (R) R[s] = sp->h_R[s];
+    if (G) G[s] = sp->h_Gs[s];
+  }
+  return FOCK_OK;
 }
 
 fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, double schwarz_thresh, double out[10]) {

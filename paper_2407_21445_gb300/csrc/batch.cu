@@ -328,6 +328,7 @@ extern "C" fock_status fock_build_jk_batched(const fock_shellpairs *const *bases
   for (int i = 0; i < nmol; ++i) {
     if (!bases[i] || !D[i] || !J[i] || !K[i]) return FOCK_ERR_INVALID_ARG;
     if (!same_opts(bases[0], bases[i])) return FOCK_ERR_INVALID_ARG;
+    if (bases[i]->opts.k_mode != FOCK_K_EXACT) return FOCK_ERR_INVALID_ARG;  // exact exchange test only
   }
   if (!(schwarz_thresh >= bases[0]->tau_build) || !isfinite(schwarz_thresh)) return FOCK_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);

@@ -20,6 +20,18 @@ __device__ __forceinline__ double f2d_pos(float f) {
   return __longlong_as_double((long long)((e << 52) | (m << 29)));
 }
 
+// Exact float -> double on the integer units for any finite float
+// (zero and subnormal inputs map to 0, |x| < 1.2e-38).
+__device__ __forceinline__ double f2d_any(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long e = ex + (1023u - 127u);
+  const unsigned long long m = u & 0x7fffffu;
+  return __longlong_as_double((long long)(sign | (e << 52) | (m << 29)));
+}
+
 // 1/sqrt(s) for s > 0 in double precision: FP32 seed y0 = rsqrtf(s_f), then
 // one third-order Householder step of the Newton iteration for 1/sqrt
 // (error e = 1 - s y0^2, y = y0 (1 + e/2 + 3e^2/8)); the seed's relative
@@ -90,13 +102,52 @@ __device__ __forceinline__ double boys_taylor(const double *__restrict__ tab, in
   return fma(f, x, c01.x);
 }
 
-// Seeds pref (-2 alpha)^m F_m(T), m = 0..L, into out[] (compile-time L).
+// x rounded toward zero to FP32 on the integer units (|x| < 2^-126 gives 0);
+// used for the Taylor variable, |x| <= h/2.
+__device__ __forceinline__ float d2f_small(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ffu) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  const unsigned sign = (unsigned)(u >> 63) << 31;
+  return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+}
+
+// The same Taylor polynomial with its four highest terms on the FP32 units:
+// with |x| <= h/2 = 1/32 and F_{m+k} <= F_m, the terms k >= 4 add at most
+// (1/32)^4/4! F_m = 4e-8 F_m, so their FP32 rounding (and the FP32 copies of
+// c4..c7 and of x) perturbs F_m by about 1e-14 relative, while four FP64
+// fused multiply-adds are saved per order.  tabf is the FP32 copy of the
+// table (same layout); c4..c7 are its entry's second 16 bytes.
+__device__ __forceinline__ double boys_taylor_split(const double *__restrict__ tab, const float *__restrict__ tabf,
+                                                    int gi, int m, double x, float xf) {
+  const size_t ent = ((size_t)gi * (LTOT + 1) + m) * BOYS_TAYLOR;
+  const double2 *c = reinterpret_cast<const double2 *>(tab + ent);
+  const double2 c23 = __ldg(c + 1), c01 = __ldg(c);
+  const float4 h = __ldg(reinterpret_cast<const float4 *>(tabf + ent) + 1);
+  float t = fmaf(h.w, xf, h.z);
+  t = fmaf(t, xf, h.y);
+  t = fmaf(t, xf, h.x);
+  double f = fma(f2d_any(t), x, c23.y);
+  f = fma(f, x, c23.x);
+  f = fma(f, x, c01.y);
+  return fma(f, x, c01.x);
+}
+
+// Seeds pref (-2 alpha)^m F_m(T), m = 0..L, into out[] (compile-time L);
+// tabf (the FP32 table) selects the split evaluation.
 template <int L>
-__device__ __forceinline__ void boys_seeds(const double *__restrict__ tab, const PrimQuartet &q, double (&out)[L + 1]) {
+__device__ __forceinline__ void boys_seeds(const double *__restrict__ tab, const PrimQuartet &q, double (&out)[L + 1],
+                                           const float *__restrict__ tabf = nullptr) {
   if (q.gi >= 0) {
     const double x = q.Ti - q.T;
+    if (tabf) {
+      const float xf = d2f_small(x);
 #pragma unroll
-    for (int m = 0; m <= L; ++m) out[m] = boys_taylor(tab, q.gi, m, x);
+      for (int m = 0; m <= L; ++m) out[m] = boys_taylor_split(tab, tabf, q.gi, m, x, xf);
+    } else {
+#pragma unroll
+      for (int m = 0; m <= L; ++m) out[m] = boys_taylor(tab, q.gi, m, x);
+    }
   } else {
     // asymptotic: F_0 = sqrt(pi/T)/2, F_m = F_{m-1} (m - 1/2) / T
     const double rt = rsqrt_nh(q.T, q.Tf);
@@ -130,10 +181,11 @@ __device__ __forceinline__ void boys_eval_all(const double *__restrict__ tab, in
 // write seeds m into F[]; the lane that writes m = L also writes R0[0].
 template <int G>
 __device__ __forceinline__ void boys_seeds_rt(const double *__restrict__ tab, const PrimQuartet &q, int L, double *F,
-                                              double *R0, int gl) {
+                                              double *R0, int gl, const float *__restrict__ tabf = nullptr) {
   if constexpr (G == 1) {
     double c = q.pref, prev = 0.0;
     const double x = q.Ti - q.T;
+    const float xf = d2f_small(x);
     double rt = 0.0, it = 0.0;
     if (q.gi < 0) {
       rt = rsqrt_nh(q.T, q.Tf);
@@ -142,7 +194,7 @@ __device__ __forceinline__ void boys_seeds_rt(const double *__restrict__ tab, co
     for (int m = 0; m <= L; ++m) {
       double f;
       if (q.gi >= 0)
-        f = boys_taylor(tab, q.gi, m, x);
+        f = tabf ? boys_taylor_split(tab, tabf, q.gi, m, x, xf) : boys_taylor(tab, q.gi, m, x);
       else
         f = (m == 0) ? 0.88622692545275801365 * rt : prev * ((m - 0.5) * it);
       prev = f;
@@ -154,7 +206,8 @@ __device__ __forceinline__ void boys_seeds_rt(const double *__restrict__ tab, co
   for (int m = gl; m <= L; m += G) {
     double f;
     if (q.gi >= 0) {
-      f = boys_taylor(tab, q.gi, m, q.Ti - q.T);
+      const double x = q.Ti - q.T;
+      f = tabf ? boys_taylor_split(tab, tabf, q.gi, m, x, d2f_small(x)) : boys_taylor(tab, q.gi, m, x);
     } else {
       const double rt = rsqrt_nh(q.T, q.Tf), it = rt * rt;
       f = 0.88622692545275801365 * rt;
@@ -168,17 +221,6 @@ __device__ __forceinline__ void boys_seeds_rt(const double *__restrict__ tab, co
   }
 }
 
-// Exact float -> double on the integer units for any finite float
-// (zero and subnormal inputs map to 0, |x| < 1.2e-38).
-__device__ __forceinline__ double f2d_any(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ex = (u >> 23) & 0xffu;
-  if (ex == 0) return 0.0;
-  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  const unsigned long long e = ex + (1023u - 127u);
-  const unsigned long long m = u & 0x7fffffu;
-  return __longlong_as_double((long long)(sign | (e << 52) | (m << 29)));
-}
 
 // FP32 seeds pref (-2 alpha)^m F_m(T), m = 0..L: six Taylor terms from the
 // FP32 copy of the table (truncation < 2e-12 relative) or the asymptotic form.

@@ -91,6 +91,9 @@ struct DevPairs {
   const float *Uf;     // U as above, FP32
   const float *Ef;     // Hermite coefficients, FP32
   const int *smol;     // shell -> molecule of a batch (null for one molecule)
+  const int *satom;    // shell -> atom (shells on one atom share an index)
+  const float *Gn;     // nshell^2: n_z G_xz for kept pairs (x, z), else 0 (GDG bound)
+  const float2 *sRG;   // per shell: radius R_s and largest Schwarz factor G_s of its kept pairs
   int nshell, nbf, npair;
   int nprim_total;
   long long nE_total;
@@ -125,6 +128,9 @@ struct Staging {
   std::vector<float4> paf;
   std::vector<float> Uf, Ef, Gf, shl;
   std::vector<int> smol;
+  std::vector<int> satom;
+  std::vector<float2> sRG;
+  std::vector<float> Gn;
 };
 
 // One unit of work: bra pair index, ket pair index range [k0, k1).
@@ -143,6 +149,8 @@ struct Tier {
   int warps_per_block;
   int blocks;           // persistent grid
   size_t smem;          // dynamic shared memory per block
+  int blocks32 = 0;     // the same for the FP32 part of a mixed group tier,
+  size_t smem32 = 0;    // whose scratch needs half the bytes (floats)
   int nunits;
   Unit *d_units;
 };
@@ -164,6 +172,8 @@ struct fock_shellpairs {
   std::vector<fk::Unit> h_units;      // all tiers, concatenated
   std::vector<int> h_unit_tier;
   fk::Staging host;                   // compact pair data (merged into batch plans)
+  std::vector<double> h_R, h_Gs;      // per-shell radius and Schwarz maximum (decay bound)
+  int decay_nbins = 0;                // 0.5-bohr distance bins of the decay fit
   unsigned long long serial = 0;      // unique id (batch plan cache key)
   // device allocations
   void *d_block = nullptr;            // one allocation holding all pair arrays
@@ -173,6 +183,16 @@ struct fock_shellpairs {
 };
 
 namespace fk {
+// Byte offsets of the per-call scratch of a J/K build in one buffer (256-byte
+// aligned parts): shell-block maxima (FP64) at 0, work counters, the FP32
+// copy of D (mixed precision), FP32 block maxima, and in the decay-bound
+// exchange mode the bounds W, the distance bins and H, Lambda.  (api.cu)
+struct ScratchLayout {
+  size_t cnt_off = 0, df_off = 0, dshf_off = 0, w_off = 0, bins_off = 0, hl_off = 0, t_off = 0, gdg_off = 0,
+         total = 0;
+};
+ScratchLayout scratch_layout(const fock_shellpairs *sp);
+
 // Status of a CUDA runtime result; a failure also sets the text returned by
 // fock_last_error ("where: error name (description)").  (api.cu)
 fock_status cuda_status(cudaError_t e, const char *where);
@@ -188,6 +208,15 @@ int hermite_count(int la, int lb);
 void hermite_pair(int la, int lb, double alpha, const double *A, double beta, const double *B,
                   bool cart_norm, double *out);
 
+// Per-call choices of a J/K build besides precision: which matrices are built
+// (1 = J, 2 = K, 3 = both) and the decay-bound exchange test (Wsh null: the
+// exact test).
+struct CallParts {
+  int parts = 3;
+  const float *Wsh = nullptr;  // nshell^2 decay bounds of the density blocks
+  double k_thresh = 0.0;       // tau*
+};
+
 // device entry points (kernels.cu)
 cudaError_t upload_tables(cudaStream_t st);
 const double *dev_boys();
@@ -202,7 +231,17 @@ cudaError_t launch_dprep(const double *D, int nbf, const int *sbf, const int *sl
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh,
                            double tau, double prim_eps, double *J, double *K, int *counter, int *counter2,
                            cudaStream_t st, const float *Df = nullptr, double fp32_cutoff = 0.0,
-                           const float *Dshf = nullptr);
+                           const float *Dshf = nullptr, const CallParts &cp = CallParts());
+// Decay bound of Sec. 4.3.1 for one density: bins (nbins doubles, zeroed
+// here) of the block maxima Dsh of shells on different atoms by centre
+// distance (0.5 bohr), the fit into HL[0] = H, HL[1] = Lambda, and the
+// per-shell-pair bounds W (nshell^2 floats; null = fit only).  With Gn
+// (nshell^2 floats, n_z G_xz over kept pairs), the FP32 block maxima Dshf and
+// two nshell^2 float buffers T, GDG, blocks whose GDG bound is below
+// k_thresh get W = 0.
+cudaError_t launch_decay_bound(const DevPairs &dp, const double *Dsh, int nbins, double *bins, double *HL, float *W,
+                               cudaStream_t st, const float *Gn = nullptr, const float *Dshf = nullptr,
+                               float *T = nullptr, float *GDG = nullptr, double k_thresh = 0.0);
 cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st);
 // batched variants (one launch over every molecule of a batch)
 cudaError_t launch_zero_batch(const MolEntry *mt, const long long *n2_prefix, int nmol, long long total,

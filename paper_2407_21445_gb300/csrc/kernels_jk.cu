@@ -26,6 +26,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "kargs.cuh"
 #include "reg_dispatch.h"
@@ -61,6 +63,10 @@ static ClassTables *s_tabs[64];
 
 static_assert(sizeof(ClassTables) % 16 == 0, "table copy uses whole 4-byte words");
 constexpr int TAB_BYTES = (int)sizeof(ClassTables);
+
+// Scratch stride (in doubles) of a group running the FP32 body: its
+// intermediates take half the bytes; kept odd for the shared-memory banks.
+__host__ __device__ constexpr int fp32_stride(int stride) { return ((stride + 1) / 2) | 1; }
 
 __device__ __forceinline__ void group_sync(unsigned mask, int G) {
   if (G > 1) __syncwarp(mask);
@@ -185,11 +191,10 @@ __device__ __forceinline__ void ket_transform(const ClassTables &ct, const Real 
   }
 }
 
-// Bra transform ERI[ab][cd] += sum_p E^{ab}_p Yh[p][cd], computed in Real and
-// added into eri (Acc = Real, or FP64 for the FP32 tail of an FP64 quartet:
-// the FP32 sum converted exactly, then one FP64 add).
-template <int G, class Real, class Acc>
-__device__ __forceinline__ void bra_transform(const ClassTables &ct, const Real *EP, const Real *Yh, Acc *eri, int nab,
+// Bra transform ERI[ab][cd] += sum_p E^{ab}_p Yh[p][cd] (two accumulation
+// chains, even / odd v).
+template <int G, class Real>
+__device__ __forceinline__ void bra_transform(const ClassTables &ct, const Real *EP, const Real *Yh, Real *eri, int nab,
                                               int ncd, int nb, int la, int lb, int cb, int gl) {
   for (int it = gl; it < nab * ncd; it += G) {
     const int ka = it / ncd, kc = it - ka * ncd;
@@ -197,11 +202,7 @@ __device__ __forceinline__ void bra_transform(const ClassTables &ct, const Real 
     const uint8_t *ac = ct.comp[la][ia], *bc = ct.comp[lb][ib];
     const int Tx = ac[0] + bc[0], Ty = ac[1] + bc[1], Tz = ac[2] + bc[2];
     const Real *Ep = EP + ct.eoff[cb][ka];
-    Real acc0, acc1 = Real(0);
-    if constexpr (sizeof(Acc) == sizeof(Real))
-      acc0 = eri[it];
-    else
-      acc0 = Real(0);
+    Real acc0 = eri[it], acc1 = Real(0);
     int e = 0;
     for (int t = 0; t <= Tx; ++t)
       for (int u = 0; u <= Ty; ++u) {
@@ -215,37 +216,15 @@ __device__ __forceinline__ void bra_transform(const ClassTables &ct, const Real 
           ++e;
         }
       }
-    if constexpr (sizeof(Acc) == sizeof(Real))
-      eri[it] = acc0 + acc1;
-    else
-      eri[it] += f2d_any(acc0 + acc1);
+    eri[it] = acc0 + acc1;
   }
-}
-
-// FP32 Boys seeds and Hermite integrals of primitive quartet (ip | jq) with
-// pair-relative centres (P - A, Q - C and A - C as FP32 hi/lo parts).
-template <int G>
-__device__ __forceinline__ const float *prim_r_f32(const KArgs &a, const ClassTables &ct, int ip, int jq, float ACx,
-                                                   float ACy, float ACz, int L, float *F, float *R0, float *R1,
-                                                   int gl, unsigned gmask) {
-  const float4 PA = a.dp.paf[ip], QC = a.dp.paf[jq];
-  const float X = PA.x - QC.x + ACx, Y = PA.y - QC.y + ACy, Z = PA.z - QC.z + ACz;
-  const float rs = rsqrtf(PA.w + QC.w);
-  const float alpha = (PA.w * QC.w) * (rs * rs);
-  const float T = alpha * fmaf(X, X, fmaf(Y, Y, Z * Z));
-  boys_seeds_rt_f32<G>(a.boysf, T, rs, -2.0f * alpha, L, F, R0, gl);
-  group_sync(gmask, G);
-  return hermite_r<G, float>(ct, L, X, Y, Z, F, R0, R1, gl, gmask);
 }
 
 // One contracted quartet on a group of G lanes, in FP64 (Real = double) or
 // in FP32 (Real = float, the mixed-precision path below the cutoff: FP32
 // table, pair-relative centres, FP32 copies of U, E and D, exact FP32->FP64
 // conversion of every digested element before the FP64 atomic add).
-// TAIL (FP64 part of a mixed build): primitive quartets whose own bound
-// G_[ab] G_[cd] Dmax is below the FP32 cutoff are left out of the FP64 loops
-// and evaluated afterwards in FP32 (prim_fp32), into the same FP64 ERIs.
-template <int G, class Real, bool TAIL = false>
+template <int G, class Real>
 __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_d, int P, int Q, int gl,
                              unsigned gmask, const MolView &mv) {
   constexpr bool F32 = sizeof(Real) == 4;
@@ -258,7 +237,9 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
   const int nab = na * nb, ncd = nc * nd;
   const int Lab = la + lb, Lcd = lc + ld, L = Lab + Lcd;
   const int nhab = nherm(Lab), nhL = nherm(L);
-  FK_CHECK(nab * ncd + nhab * ncd + 2 * nhL + L + 1 <= a.stride, 1, a.stride);
+  FK_CHECK((F32 ? (nab * ncd + nhab * ncd + 2 * nhL + L + 2) / 2 : nab * ncd + nhab * ncd + 2 * nhL + L + 1) <=
+               a.stride,
+           1, a.stride);
   FK_CHECK(P >= 0 && P < dp.npair && Q >= 0 && Q < dp.npair, 2, Q);
   FK_CHECK(dp.prim[P].x >= 0 && dp.prim[P].x + dp.prim[P].y <= a.nprimtot, 3, dp.prim[P].x);
   FK_CHECK(dp.prim[Q].x >= 0 && dp.prim[Q].x + dp.prim[Q].y <= a.nprimtot, 4, dp.prim[Q].x);
@@ -293,12 +274,10 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
   const PrimScreen ps = prim_screen(a, mv, sA, sB, sC, sD);
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
     if (prim_skip(a, mv, ps, ip, pk.x)) break;
-    if (TAIL && prim_fp32(a, ps, ip, pk.x)) break;  // the rest is FP32 work (below)
     const Real *EP = Epool + dp.eoff[ip];
     for (int i = gl; i < nhab * ncd; i += G) Yh[i] = Real(0);
     for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
       if (prim_skip(a, mv, ps, ip, jq)) break;
-      if (TAIL && prim_fp32(a, ps, ip, jq)) break;
       const Real *EQ = Epool + dp.eoff[jq];
       Real X, Y, Z;
       if constexpr (F32) {
@@ -316,49 +295,16 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
         X = q.X;
         Y = q.Y;
         Z = q.Z;
-        boys_seeds_rt<G>(a.boys, q, L, F, R0, gl);
+        boys_seeds_rt<G>(a.boys, q, L, F, R0, gl, a.boysf);
       }
       group_sync(gmask, G);
       const Real *R = hermite_r<G, Real>(ct, L, X, Y, Z, F, R0, R1, gl, gmask);
       ket_transform<G, Real>(ct, EQ, R, Yh, nhab, ncd, nd, lc, ld, ck, gl);
       group_sync(gmask, G);
     }
-    bra_transform<G, Real, Real>(ct, EP, Yh, eri, nab, ncd, nb, la, lb, cb, gl);
+    bra_transform<G, Real>(ct, EP, Yh, eri, nab, ncd, nb, la, lb, cb, gl);
     group_sync(gmask, G);
   }
-  if constexpr (TAIL) {
-    if (ps.c32 > 0.0f) {
-      // the FP32 primitive quartets, in the scratch behind the ERIs viewed as
-      // floats (Yh, R0, R1, F need half the room they take in FP64)
-      const float *ha = dp.shl + 6 * sA, *hc = dp.shl + 6 * sC;
-      const float tx = (ha[0] - hc[0]) + (ha[3] - hc[3]);
-      const float ty = (ha[1] - hc[1]) + (ha[4] - hc[4]);
-      const float tz = (ha[2] - hc[2]) + (ha[5] - hc[5]);
-      float *Yf = reinterpret_cast<float *>(Yh);
-      float *R0f = Yf + nhab * ncd;
-      float *R1f = R0f + nhL;
-      float *Ff = R1f + nhL;
-      const int kend = pk.x + pk.y;
-      for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
-        if (prim_skip(a, mv, ps, ip, pk.x)) break;
-        int j0 = pk.x;
-        while (j0 < kend && !prim_fp32(a, ps, ip, j0)) ++j0;
-        if (j0 == kend || prim_skip(a, mv, ps, ip, j0)) continue;
-        for (int i = gl; i < nhab * ncd; i += G) Yf[i] = 0.0f;
-        for (int jq = j0; jq < kend; ++jq) {
-          if (prim_skip(a, mv, ps, ip, jq)) break;
-          group_sync(gmask, G);
-          const float *R = prim_r_f32<G>(a, ct, ip, jq, tx, ty, tz, L, Ff, R0f, R1f, gl, gmask);
-          ket_transform<G, float>(ct, dp.Ef + dp.eoff[jq], R, Yf, nhab, ncd, nd, lc, ld, ck, gl);
-          group_sync(gmask, G);
-        }
-        bra_transform<G, float, double>(ct, dp.Ef + dp.eoff[ip], Yf, reinterpret_cast<double *>(eri), nab, ncd, nb,
-                                        la, lb, cb, gl);
-        group_sync(gmask, G);
-      }
-    }
-  }
-
   // digestion into J and K (Sec. 2.3 eight-fold symmetry; J = Jt + Jt^T and
   // K = Kt + Kt^T are formed afterwards by the symmetrisation kernel)
   Real fac = Real(1);
@@ -391,7 +337,9 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
     }
     return s0 + s1;
   };
-  for (int o = gl; o < n6; o += G) {
+  // J outputs are o < n2, K outputs n2 <= o < n6: only the built parts
+  const int o0 = (a.parts & 1) ? 0 : n2, o1 = (a.parts & 2) ? n6 : n2;
+  for (int o = o0 + gl; o < o1; o += G) {
     Real s;
     double *dst;
     if (o < n1) {  // J_ab += (ab|cd) D_cd
@@ -462,8 +410,12 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
 // launch per part: MODE 1 takes the survivors whose bound is at least the FP32
 // cutoff (FP64 body), MODE 2 those below it (FP32 body).  Each launch holds a
 // single body, so a warp never alternates between the two.
+// The FP32 part (MODE 2) keeps its intermediates in half the shared memory of
+// the FP64 body, so more of its blocks fit on an SM; its register budget is
+// capped to match (five blocks of four warps; the FP64 bodies keep the
+// budget of four blocks, 128 registers).
 template <int G, int MODE>
-__global__ void __launch_bounds__(128) k_jk(KArgs a) {
+__global__ void __launch_bounds__(128, MODE == 2 ? 5 : 4) k_jk(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   {
     const int *src = reinterpret_cast<const int *>(a.tabs);
@@ -492,7 +444,7 @@ __global__ void __launch_bounds__(128) k_jk(KArgs a) {
         if constexpr (MODE == 2)
           quartet_body<G, float>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
         else
-          quartet_body<G, double, MODE == 1>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
+          quartet_body<G, double>(a, ct, scr, P, q[i + grp], gl, gmask, mv);
       }
     __syncwarp();
     const int rest = n - k;  // < NG <= 32 entries move to the front
@@ -626,9 +578,191 @@ __global__ void k_dprep(const double *__restrict__ D, int N, const int *__restri
   if (Dshf) Dshf[idx] = bad ? INFINITY : (float)mx;
 }
 
+// --------------------------------------------------------------------------
+// Decay bound of the density (Sec. 4.3.1, Eq. density_bound)
+// --------------------------------------------------------------------------
+// Centre distance of shells a and b, rounded the same way as a plain
+// left-to-right evaluation (no fused multiply-adds), so that the 0.5-bohr bin
+// of a pair is reproducible by any IEEE implementation.
+__device__ __forceinline__ double centre_distance(const double *xyz, int a, int b) {
+  const double dx = __dsub_rn(xyz[3 * a], xyz[3 * b]);
+  const double dy = __dsub_rn(xyz[3 * a + 1], xyz[3 * b + 1]);
+  const double dz = __dsub_rn(xyz[3 * a + 2], xyz[3 * b + 2]);
+  return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+
+constexpr double DECAY_BIN = 0.5;  // bohr
+
+// Largest shell-block maximum of |D| per distance bin, over pairs of shells on
+// different atoms (same-atom elements would skew the decay, Sec. 4.3.1).
+// Non-negative doubles order like their bit patterns, so the maximum is an
+// integer atomicMax.
+__global__ void k_decay_bins(DevPairs dp, const double *__restrict__ Dsh, int nbins,
+                             unsigned long long *__restrict__ bins) {
+  const int ns = dp.nshell;
+  const long long n = (long long)ns * ns;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / ns), b = (int)(idx - (long long)a * ns);
+    if (b <= a || dp.satom[a] == dp.satom[b]) continue;
+    const double v = Dsh[idx];
+    if (!(v > 0.0) || !isfinite(v)) continue;
+    int k = (int)floor(centre_distance(dp.sxyz, a, b) / DECAY_BIN);
+    if (k >= nbins) k = nbins - 1;
+    atomicMax(bins + k, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+// Least-squares line ln max|D| = ln H - Lambda r through the non-empty bins
+// (r the bin centre), then ln H raised so that the line lies above each bin's
+// maximum over the whole bin (its far edge when Lambda > 0).  Fewer than two
+// bins: Lambda = 0, H the largest maximum.  One block.
+__global__ void k_decay_fit(const unsigned long long *__restrict__ bins, int nbins, double *__restrict__ HL) {
+  __shared__ double red[5][256];
+  double n = 0, sx = 0, sy = 0, sxx = 0, sxy = 0;
+  for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
+    const double v = __longlong_as_double((long long)bins[i]);
+    if (!(v > 0.0)) continue;
+    const double x = (i + 0.5) * DECAY_BIN, y = log(v);
+    n += 1;
+    sx += x;
+    sy += y;
+    sxx += x * x;
+    sxy += x * y;
+  }
+  red[0][threadIdx.x] = n;
+  red[1][threadIdx.x] = sx;
+  red[2][threadIdx.x] = sy;
+  red[3][threadIdx.x] = sxx;
+  red[4][threadIdx.x] = sxy;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 5; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  n = red[0][0];
+  sx = red[1][0];
+  sy = red[2][0];
+  sxx = red[3][0];
+  sxy = red[4][0];
+  double lam = 0.0;
+  if (n >= 2.0) {
+    const double den = n * sxx - sx * sx;
+    if (den > 0.0) lam = -(n * sxy - sx * sy) / den;
+  }
+  __syncthreads();
+  // ln H = max over bins of y + Lambda * edge
+  double m = -INFINITY;
+  for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
+    const double v = __longlong_as_double((long long)bins[i]);
+    if (!(v > 0.0)) continue;
+    const double edge = (lam > 0.0 ? i + 1 : i) * DECAY_BIN;
+    m = fmax(m, log(v) + lam * edge);
+  }
+  red[0][threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    HL[0] = red[0][0] == -INFINITY ? 0.0 : exp(red[0][0]);
+    HL[1] = lam;
+  }
+}
+
+// C = A B (transB = 0) or A B^T (transB = 1) for n x n row-major FP32
+// matrices: 32 x 32 output tiles, 16 x 16 threads with 2 x 2 outputs each,
+// K steps of 32 staged in shared memory; ragged edges read as zero.
+__global__ void k_sgemm_nn(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C, int n,
+                           int transB) {
+  __shared__ float As[32][33], Bs[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int i = ty; i < 32; i += 16)
+      for (int j = tx; j < 32; j += 16) {
+        const int r = r0 + i, k = k0 + j;
+        As[i][j] = (r < n && k < n) ? A[(size_t)r * n + k] : 0.f;
+        const int kb = k0 + i, c = c0 + j;
+        Bs[i][j] = (kb < n && c < n) ? (transB ? B[(size_t)c * n + kb] : B[(size_t)kb * n + c]) : 0.f;
+      }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float a0 = As[ty][k], a1 = As[ty + 16][k], b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+      acc[0][0] = fmaf(a0, b0, acc[0][0]);
+      acc[0][1] = fmaf(a0, b1, acc[0][1]);
+      acc[1][0] = fmaf(a1, b0, acc[1][0]);
+      acc[1][1] = fmaf(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
+      if (r < n && c < n) C[(size_t)r * n + c] = acc[i][j];
+    }
+}
+
+// W_xy = H exp(-Lambda (|XY| - R_x - R_y)): for every kept pair (x z) and
+// (y w), |ZW| >= |XY| - R_x - R_y, so W_xy bounds |D_zw|.  Where that distance
+// bound is not positive the partners may share an atom (elements the fit
+// excludes) and no bound is used (+inf).
+// With GDG (the block bound (A Dsh A^T)_xy >= max |K_xy|, A_xz = n_z G_xz
+// over kept pairs, Sec. 4.3.1's comparison with Luehr et al.) below tau*, the
+// whole block K_xy is negligible and W_xy = 0 drops its contributions.
+__global__ void k_decay_w(DevPairs dp, const double *__restrict__ HL, const float *__restrict__ GDG, float kthr,
+                          float *__restrict__ W) {
+  const int ns = dp.nshell;
+  const long long n = (long long)ns * ns;
+  const double H = HL[0], lam = HL[1];
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(idx / ns), y = (int)(idx - (long long)x * ns);
+    const double r = centre_distance(dp.sxyz, x, y) - (double)dp.sRG[x].x - (double)dp.sRG[y].x;
+    float w = r > 0.0 ? (float)(H * exp(-lam * r)) : INFINITY;
+    // FP32 sums of non-negative terms: a relative margin of 1e-4 covers
+    // their rounding, so the test only drops blocks the exact bound drops
+    if (GDG && fmaxf(GDG[idx], GDG[(long long)y * ns + x]) * 1.0001f < kthr) w = 0.0f;
+    W[idx] = w;
+  }
+}
+
+cudaError_t launch_decay_bound(const DevPairs &dp, const double *Dsh, int nbins, double *bins, double *HL, float *W,
+                               cudaStream_t st, const float *Gn, const float *Dshf, float *T, float *GDG,
+                               double k_thresh) {
+  if (nbins < 1 || !dp.satom || !dp.sRG) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(double) * nbins, st);
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)dp.nshell * dp.nshell;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+  k_decay_bins<<<grid, 256, 0, st>>>(dp, Dsh, nbins, reinterpret_cast<unsigned long long *>(bins));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_decay_fit<<<1, 256, 0, st>>>(reinterpret_cast<const unsigned long long *>(bins), nbins, HL);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !W) return e;
+  const bool gdg = Gn && Dshf && T && GDG;
+  if (gdg) {
+    const int ns = dp.nshell;
+    dim3 blk(16, 16), grd((ns + 31) / 32, (ns + 31) / 32);
+    k_sgemm_nn<<<grd, blk, 0, st>>>(Gn, Dshf, T, ns, 0);    // T = A Dsh
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sgemm_nn<<<grd, blk, 0, st>>>(T, Gn, GDG, ns, 1);     // GDG = T A^T
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_decay_w<<<grid, 256, 0, st>>>(dp, HL, gdg ? GDG : nullptr, (float)k_thresh, W);
+  return cudaGetLastError();
+}
+
 // M <- M + M^T in place, for J (z = 0) and K (z = 1).
 __global__ void k_symmetrize(double *J, double *K, int n) {
-  double *M = blockIdx.z == 0 ? J : K;
+  double *M = (blockIdx.z == 0 && J) ? J : K;  // J or K may be absent (one z slice)
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n || i > j) return;
@@ -812,7 +946,9 @@ cudaError_t launch_dprep(const double *D, int nbf, const int *sbf, const int *sl
 }
 
 cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st) {
-  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8, 2);
+  const int nz = (J ? 1 : 0) + (K ? 1 : 0);
+  if (nz == 0) return cudaSuccess;
+  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8, nz);
   k_symmetrize<<<grd, blk, 0, st>>>(J, K, n);
   return cudaGetLastError();
 }
@@ -835,7 +971,8 @@ static cudaError_t launch_g(const Tier &t, KArgs a, int threads, cudaStream_t st
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     a.counter = counter2;
-    k_jk<G, 2><<<t.blocks, threads, t.smem, st>>>(a);
+    a.stride = fp32_stride(t.stride);  // scratch counted in doubles, half of them needed
+    k_jk<G, 2><<<t.blocks32 > 0 ? t.blocks32 : t.blocks, threads, t.smem32 > 0 ? t.smem32 : t.smem, st>>>(a);
   } else {
     k_jk<G, 0><<<t.blocks, threads, t.smem, st>>>(a);
   }
@@ -857,6 +994,7 @@ static cudaError_t launch_group(const Tier &t, const KArgs &a, int threads, cuda
 template <int G>
 static cudaError_t configure_g(Tier &t) {
   const size_t per_warp = (size_t)(32 / G) * t.stride * sizeof(double);
+  const size_t per_warp32 = (size_t)(32 / G) * fp32_stride(t.stride) * sizeof(double);
   // 227 KB per block, less the kernel's static work queues
   const size_t limit = 227 * 1024 - sizeof(int) * 4 * 64;
   int wpb = 4;
@@ -876,6 +1014,14 @@ static cudaError_t configure_g(Tier &t) {
   t.blocks = nsm * per_sm;
   const int need = (t.nunits + wpb - 1) / wpb;
   if (t.blocks > need) t.blocks = need > 0 ? need : 1;
+  // FP32 part of a mixed tier: same warps per block, half the scratch
+  t.smem32 = TAB_BYTES + wpb * per_warp32;
+  int per_sm32 = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_jk<G, 2>, 32 * wpb, t.smem32);
+  if (e != cudaSuccess) return e;
+  if (per_sm32 < 1) per_sm32 = 1;
+  t.blocks32 = nsm * per_sm32;
+  if (t.blocks32 > need) t.blocks32 = need > 0 ? need : 1;
   return cudaSuccess;
 }
 
@@ -920,7 +1066,11 @@ static cudaError_t set_group_smem(const Tier &t) {
   return cudaErrorInvalidValue;
 }
 
-static void set_screen_args(KArgs &a, double tau, const float *Dshf, double prim_eps) {
+static void set_screen_args(KArgs &a, double tau, const float *Dshf, double prim_eps,
+                            const CallParts &cp = CallParts()) {
+  a.parts = cp.parts;
+  a.Wsh = cp.Wsh;
+  a.k_thresh_f = (float)cp.k_thresh;
   a.Dshf = Dshf;
   a.tau_lo = (float)(tau * (1.0 - 1e-4));
   a.tau_hi = (float)(tau * (1.0 + 1e-4));
@@ -930,7 +1080,7 @@ static void set_screen_args(KArgs &a, double tau, const float *Dshf, double prim
 
 cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, const double *Dsh, double tau,
                            double prim_eps, double *J, double *K, int *counter, int *counter2, cudaStream_t st,
-                           const float *Df, double fp32_cutoff, const float *Dshf) {
+                           const float *Df, double fp32_cutoff, const float *Dshf, const CallParts &cp) {
   if (t.nunits == 0) return cudaSuccess;
   if (t.reg_cb >= 0) {
     KArgs a;
@@ -953,7 +1103,7 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
     a.fp32_cutoff_f = (float)a.fp32_cutoff;
     a.Df = Df;
     a.boysf = dev_boys_f();
-    set_screen_args(a, tau, Dshf, prim_eps);
+    set_screen_args(a, tau, Dshf, prim_eps, cp);
     return launch_reg(t.reg_cb, t.reg_ck, a, t.blocks, 32 * t.warps_per_block, st);
   }
   cudaError_t ae = set_group_smem(t);
@@ -978,7 +1128,7 @@ cudaError_t launch_jk_tier(const Tier &t, const DevPairs &dp, const double *D, c
   a.fp32_cutoff_f = (float)a.fp32_cutoff;
   a.Df = Df;
   a.boysf = dev_boys_f();
-  set_screen_args(a, tau, Dshf, prim_eps);
+  set_screen_args(a, tau, Dshf, prim_eps, cp);
   return launch_group(t, a, 32 * t.warps_per_block, st, counter2);
 }
 

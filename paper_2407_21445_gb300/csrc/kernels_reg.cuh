@@ -225,7 +225,7 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &m
   };
   sfor<NAB * NCD>([&](auto i) { eri_at(FK_CI(i)) = 0.0; });
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
-  const PrimScreen ps = prim_screen(a, mv, sA, sB, sC, sD);
+  const PrimScreen ps = prim_screen<MIXED>(a, mv, sA, sB, sC, sD);
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
     if (prim_skip(a, mv, ps, ip, pk.x)) break;  // weaker bra primitives follow
     if (MIXED && prim_fp32(a, ps, ip, pk.x)) break;  // the rest is FP32 work (below)
@@ -238,7 +238,7 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &m
       if (MIXED && prim_fp32(a, ps, ip, jq)) break;
       const PrimQuartet q = prim_quartet(P4, Pf, dp.pz[jq], dp.pf[jq]);
       double F[L + 1];
-      boys_seeds<L>(a.boys, q, F);
+      boys_seeds<L>(a.boys, q, F, a.boysf);
       double R[NHL];
       hermite_r_reg<L, double>(F, q.X, q.Y, q.Z, R);
       // ket transform: Y[p][cd] += sum_q (-1)^{|q|} E^{cd}_q R_{p+q}
@@ -300,6 +300,7 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &m
   double *__restrict__ Km = mv.K;
   auto E4 = [&](int ia, int ib, int ic, int id) -> double { return eri_at((ia * NB + ib) * NCD + ic * ND + id); };
   auto Dv = [&](int r, int c) -> double { return __ldg(Dm + (size_t)r * N + c); };
+  if (!MIXED || (a.parts & 1)) {
   sfor<NAB>([&](auto k) {  // J_ab += (ab|cd) D_cd
     constexpr int ia = FK_CI(k) / NB, ib = FK_CI(k) % NB;
     double s = 0.0;
@@ -312,6 +313,8 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &m
     sfor<NAB>([&](auto m) { s = fma(E4(FK_CI(m) / NB, FK_CI(m) % NB, ic, id), Dv(fa + FK_CI(m) / NB, fb + FK_CI(m) % NB), s); });
     atomicAdd(Jm + (size_t)(fc + ic) * N + fd + id, fac2 * s);
   });
+  }
+  if (MIXED && !(a.parts & 2)) return;
   sfor<NA * NC>([&](auto k) {  // K_ac += (ab|cd) D_bd
     constexpr int ia = FK_CI(k) / NC, ic = FK_CI(k) % NC;
     double s = 0.0;
@@ -425,6 +428,7 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
   double *__restrict__ Km = mv.K;
   auto E4 = [&](int ia, int ib, int ic, int id) -> float { return eri[(ia * NB + ib) * NCD + ic * ND + id]; };
   auto Dv = [&](int r, int c) -> float { return __ldg(Dm + (size_t)r * N + c); };
+  if (a.parts & 1) {
   sfor<NAB>([&](auto k) {
     constexpr int ia = FK_CI(k) / NB, ib = FK_CI(k) % NB;
     float s = 0.0f;
@@ -437,6 +441,8 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
     sfor<NAB>([&](auto m) { s = fmaf(E4(FK_CI(m) / NB, FK_CI(m) % NB, ic, id), Dv(fa + FK_CI(m) / NB, fb + FK_CI(m) % NB), s); });
     atomicAdd(Jm + (size_t)(fc + ic) * N + fd + id, f2d_any(fac2 * s));
   });
+  }
+  if (!(a.parts & 2)) return;
   sfor<NA * NC>([&](auto k) {
     constexpr int ia = FK_CI(k) / NC, ic = FK_CI(k) % NC;
     float s = 0.0f;
@@ -487,8 +493,10 @@ __device__ __forceinline__ void drain_reg(const KArgs &a, const int *qp, const i
   }
 }
 
-// MIXED = false: FP64 build (no FP32 code in the kernel); true: mixed
-// precision (FP32 quartets below the cutoff, FP32 primitive tails above it).
+// MIXED = false: the lean FP64 fused J+K build (no FP32 code, exact test
+// only); true: every feature -- mixed precision (FP32 quartets below the
+// cutoff, FP32 primitive tails above it), J-only / K-only builds and the
+// decay-bound exchange test.
 template <int LA, int LB, int LC, int LD, bool MIXED>
 __global__ void __launch_bounds__(128) k_reg(KArgs a) {
   extern __shared__ __align__(16) double reg_smem[];
@@ -525,7 +533,7 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
       float b = -1.0f;
       if (Q < un.k1) {
         const int2 cd = a.dp.ab[Q];
-        b = quartet_bound(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
+        b = quartet_bound<MIXED>(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
       }
       const bool is32 = MIXED && b >= 0.0f && b < a.fp32_cutoff_f, is64 = b >= 0.0f && !is32;
       const unsigned m64 = __ballot_sync(0xffffffffu, is64), m32 = __ballot_sync(0xffffffffu, is32);

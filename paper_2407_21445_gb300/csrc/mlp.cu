@@ -29,8 +29,6 @@ struct fock_mlp {
 
 namespace {
 
-constexpr int TS = 16;
-
 template <class T>
 __device__ __forceinline__ float ld(const T *p) {
   return (float)(*p);
@@ -40,41 +38,109 @@ __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16 *p) {
   return __bfloat162float(*p);
 }
 
+// Round an FP32 value to TF32 (10-bit mantissa, round to nearest away) and
+// return it as its 32-bit pattern, the operand format of mma .tf32.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// D = A B + C for one m16n8k8 tile on the tensor cores (TF32 inputs, FP32
+// accumulation; fragment layouts of the PTX ISA for mma.m16n8k8 .tf32).
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 // C[m][n] (+)= sum_k A(m,k) B(k,n); A(m,k) = TA ? A[k*lda+m] : A[m*lda+k],
-// B(k,n) = TB ? B[n*ldb+k] : B[k*ldb+n].  16x16 tiles staged in shared
-// memory, FP32 accumulation.  Optional epilogue: + bias[n], store pre- and
-// post-SiLU values.
+// B(k,n) = TB ? B[n*ldb+k] : B[k*ldb+n], on the tensor cores: a block of four
+// warps owns a 64 x 64 tile of C (each warp 32 x 32, 2 x 4 mma tiles), K in
+// steps of 16 staged in shared memory as FP32.  Each operand is split into a
+// TF32 high part and a TF32 remainder, and the three products hi*hi, hi*lo,
+// lo*hi are accumulated in FP32, which keeps the product accurate to about
+// FP32 rounding (BF16 weights are exact in TF32, so their remainder is zero).
+// Optional epilogue: + bias[n], store pre- and post-SiLU values.
+constexpr int GT = 64, GK = 16;
 template <bool TA, bool TB, class TAt, class TBt>
-__global__ void k_gemm(int M, int N, int K, const TAt *__restrict__ A, int lda, const TBt *__restrict__ B, int ldb,
-                       float *__restrict__ C, int ldc, int accumulate, const float *__restrict__ bias,
-                       float *__restrict__ act) {
-  __shared__ float As[TS][TS + 1], Bs[TS][TS + 1];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int row = blockIdx.y * TS + ty, col = blockIdx.x * TS + tx;
-  float acc = 0.0f;
-  for (int k0 = 0; k0 < K; k0 += TS) {
-    {
-      const int m = blockIdx.y * TS + ty, k = k0 + tx;
-      As[ty][tx] = (m < M && k < K) ? ld(TA ? A + (size_t)k * lda + m : A + (size_t)m * lda + k) : 0.0f;
-    }
-    {
-      const int k = k0 + ty, n = blockIdx.x * TS + tx;
-      Bs[ty][tx] = (k < K && n < N) ? ld(TB ? B + (size_t)n * ldb + k : B + (size_t)k * ldb + n) : 0.0f;
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const TAt *__restrict__ A, int lda,
+                                              const TBt *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
+                                              int accumulate, const float *__restrict__ bias, float *__restrict__ act) {
+  __shared__ float As[GT][GK + 4];  // [m][k]
+  __shared__ float Bs[GT][GK + 4];  // [n][k]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int i = tid; i < GT * GK; i += 128) {
+      const int r = i / GK, k = i - r * GK;  // k fastest: row-major reads of A and B^T
+      const int m = m0 + r, n = n0 + r, kk = k0 + k;
+      As[r][k] = (m < M && kk < K) ? ld(TA ? A + (size_t)kk * lda + m : A + (size_t)m * lda + kk) : 0.0f;
+      Bs[r][k] = (n < N && kk < K) ? ld(TB ? B + (size_t)n * ldb + kk : B + (size_t)kk * ldb + n) : 0.0f;
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < TS; ++kk) acc = fmaf(As[ty][kk], Bs[kk][tx], acc);
+    for (int ks = 0; ks < GK; ks += 8) {
+      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + 16 * i + g;
+        const float v[4] = {As[r][ks + t], As[r + 8][ks + t], As[r][ks + t + 4], As[r + 8][ks + t + 4]};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ah[i][q] = to_tf32(v[q]);
+          al[i][q] = to_tf32(v[q] - __uint_as_float(ah[i][q]));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + 8 * j + g;
+        const float v[2] = {Bs[c][ks + t], Bs[c][ks + t + 4]};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          bh[j][q] = to_tf32(v[q]);
+          bl[j][q] = to_tf32(v[q] - __uint_as_float(bh[j][q]));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          mma_tf32(acc[i][j], al[i], bh[j]);
+          mma_tf32(acc[i][j], ah[i], bl[j]);
+          mma_tf32(acc[i][j], ah[i], bh[j]);
+        }
+    }
     __syncthreads();
   }
-  if (row < M && col < N) {
-    if (bias) acc += bias[col];
-    float *c = C + (size_t)row * ldc + col;
-    *c = accumulate ? *c + acc : acc;
-    if (act) {
-      const float s = 1.0f / (1.0f + __expf(-acc));
-      act[(size_t)row * ldc + col] = acc * s;
-    }
-  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int row = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0), col = n0 + wn + 8 * j + 2 * t + (r & 1);
+        if (row >= M || col >= N) continue;
+        float v = acc[i][j][r];
+        if (bias) v += bias[col];
+        float *c = C + (size_t)row * ldc + col;
+        *c = accumulate ? *c + v : v;
+        if (act) {
+          const float s = 1.0f / (1.0f + __expf(-v));
+          act[(size_t)row * ldc + col] = v * s;
+        }
+      }
 }
 
 // d = dA * silu'(z)
@@ -133,8 +199,8 @@ int blocks_for(long long n) {
 template <bool TA, bool TB, class TAt, class TBt>
 cudaError_t gemm(int M, int N, int K, const TAt *A, int lda, const TBt *B, int ldb, float *C, int ldc, int acc,
                  const float *bias, float *act, cudaStream_t st) {
-  dim3 blk(TS, TS), grd((N + TS - 1) / TS, (M + TS - 1) / TS);
-  k_gemm<TA, TB, TAt, TBt><<<grd, blk, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, acc, bias, act);
+  dim3 grd((N + GT - 1) / GT, (M + GT - 1) / GT);
+  k_gemm<TA, TB, TAt, TBt><<<grd, 128, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, acc, bias, act);
   return cudaGetLastError();
 }
 

@@ -41,7 +41,7 @@ class fock_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("fp32_cutoff", ctypes.c_double), ("prune_eps", ctypes.c_double),
                 ("group_override", ctypes.c_int32), ("warp_scratch", ctypes.c_int32), ("reg_max_L", ctypes.c_int32),
                 ("tune_isolate", ctypes.c_int32), ("schedule", ctypes.c_int8 * (NCLASS * NCLASS)),
-                ("reserved", ctypes.c_int8 * 4)]
+                ("k_mode", ctypes.c_int32), ("k_thresh", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -115,6 +115,8 @@ def lib() -> ctypes.CDLL:
             L.fock_hermite_count.restype = i
             L.fock_hermite_e.argtypes = [i, i, d, p, d, p, p]
             L.fock_hermite_e.restype = i
+            L.fock_decay_bound.argtypes = [p, p, p, p, p, p]
+            L.fock_decay_bound.restype = i
             L.fock_build_jk_noalloc.argtypes = [p, p, d, p, p, p]
             L.fock_build_jk_noalloc.restype = i
             L.fock_opts_size.argtypes = []
@@ -177,8 +179,10 @@ class _BasisArrays:
 
 
 def make_opts(precision=FOCK_FP64, fp32_cutoff=1e-5, prune_eps=1e-3, group_override=0, warp_scratch=0,
-              reg_max_L=0, schedule=None) -> fock_opts:
+              reg_max_L=0, schedule=None, k_mode=0, k_thresh=5e-6) -> fock_opts:
     o = fock_opts()
+    o.k_mode = k_mode
+    o.k_thresh = k_thresh
     o.reg_max_L = reg_max_L
     o.warp_scratch = warp_scratch
     o.precision = precision
@@ -219,15 +223,32 @@ def fock_kernels_per_build(handle) -> int:
     return int(lib().fock_kernels_per_build(handle))
 
 
+def _opt_tensor_ptr(t, name):
+    return None if t is None else _tensor_ptr(t, name)
+
+
 def fock_build_jk(handle, D, schwarz_thresh: float, J, K, stream=None):
-    rc = lib().fock_build_jk(handle, _tensor_ptr(D, "D"), float(schwarz_thresh), _tensor_ptr(J, "J"),
-                             _tensor_ptr(K, "K"), _stream_handle(stream))
+    """J and K of D; one of J, K may be None (only the other is built)."""
+    rc = lib().fock_build_jk(handle, _tensor_ptr(D, "D"), float(schwarz_thresh), _opt_tensor_ptr(J, "J"),
+                             _opt_tensor_ptr(K, "K"), _stream_handle(stream))
     _check(rc, "fock_build_jk")
 
 
+def fock_decay_bound(handle, D, nshell: int, stream=None):
+    """(H, Lambda, R[nshell], G[nshell]) of the density decay bound (Sec. 4.3.1)."""
+    ns = int(nshell)
+    hl = np.zeros(2)
+    R = np.zeros(ns)
+    G = np.zeros(ns)
+    rc = lib().fock_decay_bound(handle, _tensor_ptr(D, "D"), _np_ptr(hl), _np_ptr(R), _np_ptr(G),
+                                _stream_handle(stream))
+    _check(rc, "fock_decay_bound")
+    return float(hl[0]), float(hl[1]), R, G
+
+
 def fock_build_jk_noalloc(handle, D, schwarz_thresh: float, J, K, stream=None):
-    rc = lib().fock_build_jk_noalloc(handle, _tensor_ptr(D, "D"), float(schwarz_thresh), _tensor_ptr(J, "J"),
-                                     _tensor_ptr(K, "K"), _stream_handle(stream))
+    rc = lib().fock_build_jk_noalloc(handle, _tensor_ptr(D, "D"), float(schwarz_thresh), _opt_tensor_ptr(J, "J"),
+                                     _opt_tensor_ptr(K, "K"), _stream_handle(stream))
     _check(rc, "fock_build_jk_noalloc")
 
 
@@ -441,15 +462,22 @@ class JKBuilder:
         self.tau = float(schwarz_thresh)
         self.handle = fock_shellpairs_build(basis, schwarz_thresh, opts, stream)
         self.nbf = fock_nbasis(self.handle)
+        self.nshell = len(basis["l"])
 
-    def build(self, D, J=None, K=None, tau=None, stream=None):
+    def build(self, D, J=None, K=None, tau=None, stream=None, parts="jk"):
+        """J and K of D (parts "jk"), or only J ("j") or only K ("k"), the other
+        returned as None."""
         import torch
-        if J is None:
+        if J is None and "j" in parts:
             J = torch.empty_like(D)
-        if K is None:
+        if K is None and "k" in parts:
             K = torch.empty_like(D)
-        fock_build_jk(self.handle, D, self.tau if tau is None else tau, J, K, stream)
-        return J, K
+        fock_build_jk(self.handle, D, self.tau if tau is None else tau, J if "j" in parts else None,
+                      K if "k" in parts else None, stream)
+        return (J if "j" in parts else None), (K if "k" in parts else None)
+
+    def decay_bound(self, D, stream=None):
+        return fock_decay_bound(self.handle, D, self.nshell, stream)
 
     def stats(self, D_host, tau=None) -> dict:
         return fock_work_stats(self.handle, D_host, self.tau if tau is None else tau)

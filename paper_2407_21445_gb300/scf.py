@@ -6,6 +6,15 @@ fock_one_electron; the small dense linear algebra (canonical
 orthogonalisation, DIIS, FP64 eigendecomposition) uses torch.linalg on the
 GPU.  Initial guesses: superposition of atomic densities (SAD) or a density
 supplied by the caller (the learned guess of guess.py).
+
+Incremental Fock build (the paper names it as future work in Sec. 7 and notes
+in Sec. 6.1 that it was switched off in the codes it compares with): J and K
+are linear in D, so J(D_n) = J(D_m) + J(D_n - D_m).  With incremental=True
+every iteration builds J and K of the density change since the last build and
+adds them; the density-weighted screening of the library then weighs each
+quartet by |D_n - D_m|, which shrinks as the SCF converges, so ever fewer
+quartets are evaluated.  A full build every `rebuild_every` iterations
+bounds the accumulation of screening errors.
 """
 from __future__ import annotations
 
@@ -40,7 +49,7 @@ class RHF:
     """Closed-shell RHF for one molecule (Z, xyz in bohr) in a given basis."""
 
     def __init__(self, Z, xyz, basis: dict, tau: float = 1e-10, opts=None, lindep: float = 1e-7,
-                 charge: int = 0):
+                 charge: int = 0, incremental: bool = False, rebuild_every: int = 8):
         self.Z = np.asarray(Z, dtype=np.float64)
         self.xyz = np.asarray(xyz, dtype=np.float64).reshape(-1, 3)
         self.basis = basis
@@ -56,6 +65,11 @@ class RHF:
         s, U = torch.linalg.eigh(S)
         keep = s > lindep  # canonical orthogonalisation (near-linear dependence)
         self.X = U[:, keep] / torch.sqrt(s[keep])
+        self.incremental = bool(incremental)
+        self.rebuild_every = max(1, int(rebuild_every))
+        self._ref = None        # (D_m, J(D_m), K(D_m)) of the last build
+        self._since_full = 0
+        self.build_densities = []  # the density each J/K build was given (for statistics)
 
     def density_from_fock(self, F: torch.Tensor, nocc=None, occ=None) -> torch.Tensor:
         Fo = self.X.T @ F @ self.X
@@ -72,7 +86,21 @@ class RHF:
         return self.density_from_fock(self.h)
 
     def fock(self, D):
-        J, K = self.builder.build(D)
+        if not self.incremental:
+            J, K = self.builder.build(D)
+            self.build_densities.append(("full", D))
+            return self.h + J - 0.5 * K
+        if self._ref is None or self._since_full >= self.rebuild_every:
+            J, K = self.builder.build(D)
+            self._since_full = 0
+            self.build_densities.append(("full", D))
+        else:
+            dD = D - self._ref[0]
+            dJ, dK = self.builder.build(dD)
+            J, K = self._ref[1] + dJ, self._ref[2] + dK
+            self._since_full += 1
+            self.build_densities.append(("delta", dD))
+        self._ref = (D.clone(), J, K)
         return self.h + J - 0.5 * K
 
     def energy(self, D, F) -> float:

@@ -32,3 +32,16 @@ def test_mixed_peak_fraction_arithmetic():
     assert abs(r["fp64_achieved_tflops"] - 2.0) < 1e-12 and abs(r["fp32_achieved_tflops"] - 1.0) < 1e-12
     assert abs(r["combined"] - (2.0 / bench.FP64_PEAK_TFLOPS + 1.0 / bench.FP32_PEAK_TFLOPS)) < 1e-12
     assert abs(bench.FP64_PEAK_TFLOPS - 1.25856) < 1e-9
+
+
+def test_fma_probe_compiles_for_sm103a(tmp_path):
+    """The probe behind the FP64/FP32 peak figures (bench.py --fma-peak)
+    compiles for sm_103a (it runs only on a GPU)."""
+    import shutil
+    import bench
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    src = tmp_path / "probe.cu"
+    src.write_text(bench.FMA_PROBE_SRC)
+    out = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-c", str(src), "-o",
+                          str(tmp_path / "probe.o")], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]

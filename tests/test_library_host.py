@@ -165,7 +165,8 @@ def test_opts_layout_and_schedule_validation():
     device work."""
     L = fb.lib()
     assert L.fock_opts_size() == ctypes.sizeof(fb.fock_opts)
-    assert fb.fock_opts.schedule.offset == 40 and ctypes.sizeof(fb.fock_opts) == 144
+    assert fb.fock_opts.schedule.offset == 40 and fb.fock_opts.k_mode.offset == 140
+    assert fb.fock_opts.k_thresh.offset == 144 and ctypes.sizeof(fb.fock_opts) == 152
     good = molgen.problem(0).basis
     arr = _desc(good)
 
@@ -179,6 +180,9 @@ def test_opts_layout_and_schedule_validation():
     o = fk.make_opts()
     o.tune_isolate = 2
     assert build(o) == 1
+    # exchange mode: only EXACT and DECAY_BOUND, the latter with a positive tau*
+    for mode, thr in ((2, 5e-6), (-1, 5e-6), (1, 0.0), (1, -1.0), (1, float("nan"))):
+        assert build(fk.make_opts(k_mode=mode, k_thresh=thr)) == 1, (mode, thr)
     o = fk.make_opts(schedule={(5, 2): 8, 12: -1})
     assert fk.schedule_of(o) == {(2, 5): 8, (1, 2): -1}
     assert L.fock_autotune(None, 1, None, None, 1e-10, 3, None, None, None, None) == 1

@@ -32,8 +32,8 @@ def env():
 
 def _noalloc(L, torch, handle, D, tau, J, K):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    return L.fock_build_jk_noalloc(handle, ctypes.c_void_p(D.data_ptr()), tau, ctypes.c_void_p(J.data_ptr()),
-                                   ctypes.c_void_p(K.data_ptr()), stream)
+    ptr = lambda t: ctypes.c_void_p(None if t is None else t.data_ptr())  # noqa: E731
+    return L.fock_build_jk_noalloc(handle, ctypes.c_void_p(D.data_ptr()), tau, ptr(J), ptr(K), stream)
 
 
 @pytest.mark.parametrize("config,precision", [(0, 0), (1, 0), (0, 1), (1, 1)])
@@ -54,6 +54,24 @@ def test_noalloc_matches_fock_build_jk_twice(env, config, precision):
         ej = float(np.abs(J.cpu().numpy() - Jr).max())
         ek = float(np.abs(K.cpu().numpy() - Kr).max())
         assert ej <= TOL[precision] and ek <= TOL[precision], (call, ej, ek)
+    b.close()
+
+
+def test_noalloc_decay_mode_k_only_twice(env):
+    """The decay-bound exchange mode with only K requested (the fixed array
+    then also holds the bounds, the distance bins and the GDG products)."""
+    torch, fk, L = env
+    p = molgen.problem(1, carbons=12)
+    b = fk.JKBuilder(p.basis, p.tau, fk.make_opts(k_mode=1, k_thresh=5e-6))
+    D = torch.tensor(p.D, device="cuda", dtype=torch.float64)
+    _, Kr = b.build(D, parts="k")
+    torch.cuda.synchronize()
+    for call in range(2):
+        K = torch.full_like(D, float("nan"))
+        assert _noalloc(L, torch, b.handle, D, p.tau, None, K) == 0
+        torch.cuda.synchronize()
+        assert fk.fock_stream_status() == 0
+        assert float((K - Kr).abs().max()) <= TOL[0], call
     b.close()
 
 
