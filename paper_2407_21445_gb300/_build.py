@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: b
                 raise RuntimeError(f"nvcc failed for {c[-3]}")
     if force or jobs or _stale(lib_path, objs):
         tmp = lib_path + f".tmp{os.getpid()}"
-        cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+        cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             print(" ".join(cmd))

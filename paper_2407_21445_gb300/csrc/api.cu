@@ -6,9 +6,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <new>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "fock_impl.h"
@@ -888,69 +890,90 @@ fock_status fock_work_stats(const fock_shellpairs *sp, const double *D_host, dou
           mx = std::max(mx, fabs(D_host[(size_t)(sp->h_sbf[a] + i) * n + sp->h_sbf[b] + j]));
       Dsh[(size_t)a * ns + b] = mx;
     }
-  double q1 = 0, e1 = 0, q2 = 0, e2 = 0, pq = 0, fl = 0, q32 = 0, fl32 = 0;
   const double tau = schwarz_thresh;
   const bool mixed = sp->opts.precision == FOCK_MIXED && sp->opts.fp32_cutoff > 0.0;
-  for (size_t ui = 0; ui < sp->h_units.size(); ++ui) {
-    const Unit &u = sp->h_units[ui];
-    const int P = u.bra;
-    const int2 ab = sp->h_ab[P];
-    for (int Q = u.k0; Q < u.k1; ++Q) {
-      const int2 cd = sp->h_ab[Q];
-      const double g = sp->h_G[P] * sp->h_G[Q];
-      if (g < tau) continue;
-      const int la = sp->h_sl[ab.x], lb = sp->h_sl[ab.y], lc = sp->h_sl[cd.x], ld = sp->h_sl[cd.y];
-      const double ne = (double)ncart(la) * ncart(lb) * ncart(lc) * ncart(ld);
-      q1 += 1;
-      e1 += ne;
-      double dm = Dsh[(size_t)ab.x * ns + ab.y];
-      dm = std::max(dm, Dsh[(size_t)cd.x * ns + cd.y]);
-      dm = std::max(dm, Dsh[(size_t)ab.x * ns + cd.x]);
-      dm = std::max(dm, Dsh[(size_t)ab.x * ns + cd.y]);
-      dm = std::max(dm, Dsh[(size_t)ab.y * ns + cd.x]);
-      dm = std::max(dm, Dsh[(size_t)ab.y * ns + cd.y]);
-      if (g * dm < tau) continue;
-      q2 += 1;
-      e2 += ne;
-      // primitive quartets the kernels evaluate (same skip rule and order)
-      const int2 pb = sp->h_prim[P], pk = sp->h_prim[Q];
-      const double *Gp = sp->host.Gp.data();
-      const double teps = sp->prune_eps > 0.0 ? tau * sp->prune_eps : 0.0;
-      // mixed precision: inside a quartet at or above the cutoff, primitive
-      // quartets whose own bound is below it run in FP32 (the kernels decide
-      // on FP32 copies of the same numbers)
-      const bool split = mixed && !(g * dm < sp->opts.fp32_cutoff);
-      double np = 0.0, nbra = 0.0, np32 = 0.0, nbra32 = 0.0, nbra64 = 0.0;
-      for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
-        int n = 0, n32 = 0;
-        for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
-          const double x = Gp[ip] * Gp[jq] * dm;
-          if (x < teps) break;
-          ++n;
-          if (split && x < sp->opts.fp32_cutoff) ++n32;
+  const double *Gp = sp->host.Gp.data();
+  const double teps = sp->prune_eps > 0.0 ? tau * sp->prune_eps : 0.0;
+  const FlopTable &ft = flop_table();
+  // acc: quartets / ERIs passing Schwarz, evaluated quartets / ERIs, primitive
+  // quartets, modelled flops, FP32 quartets, FP32 flops
+  auto count_units = [&](size_t u0, size_t u1, double *acc) {
+    for (size_t ui = u0; ui < u1; ++ui) {
+      const Unit &u = sp->h_units[ui];
+      const int P = u.bra;
+      const int2 ab = sp->h_ab[P];
+      // the register kernels also run the primitive quartets of an FP64
+      // quartet that lie below the cutoff in FP32; the group kernels do not
+      const bool reg_tier = sp->tiers[sp->h_unit_tier[ui]].reg_cb >= 0;
+      for (int Q = u.k0; Q < u.k1; ++Q) {
+        const int2 cd = sp->h_ab[Q];
+        const double g = sp->h_G[P] * sp->h_G[Q];
+        if (g < tau) continue;
+        const int la = sp->h_sl[ab.x], lb = sp->h_sl[ab.y], lc = sp->h_sl[cd.x], ld = sp->h_sl[cd.y];
+        const double ne = (double)ncart(la) * ncart(lb) * ncart(lc) * ncart(ld);
+        acc[0] += 1;
+        acc[1] += ne;
+        double dm = Dsh[(size_t)ab.x * ns + ab.y];
+        dm = std::max(dm, Dsh[(size_t)cd.x * ns + cd.y]);
+        dm = std::max(dm, Dsh[(size_t)ab.x * ns + cd.x]);
+        dm = std::max(dm, Dsh[(size_t)ab.x * ns + cd.y]);
+        dm = std::max(dm, Dsh[(size_t)ab.y * ns + cd.x]);
+        dm = std::max(dm, Dsh[(size_t)ab.y * ns + cd.y]);
+        if (g * dm < tau) continue;
+        acc[2] += 1;
+        acc[3] += ne;
+        // primitive quartets the kernels evaluate (same skip rule and order)
+        const int2 pb = sp->h_prim[P], pk = sp->h_prim[Q];
+        const bool split = mixed && reg_tier && !(g * dm < sp->opts.fp32_cutoff);
+        double np = 0.0, nbra = 0.0, np32 = 0.0, nbra32 = 0.0, nbra64 = 0.0;
+        for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
+          int n = 0, n32 = 0;
+          for (int jq = pk.x; jq < pk.x + pk.y; ++jq) {
+            const double x = Gp[ip] * Gp[jq] * dm;
+            if (x < teps) break;
+            ++n;
+            if (split && x < sp->opts.fp32_cutoff) ++n32;
+          }
+          if (n == 0) break;
+          np += n;
+          nbra += 1;
+          np32 += n32;
+          if (n32 > 0) nbra32 += 1;
+          if (n > n32) nbra64 += 1;
         }
-        if (n == 0) break;
-        np += n;
-        nbra += 1;
-        np32 += n32;
-        if (n32 > 0) nbra32 += 1;
-        if (n > n32) nbra64 += 1;
-      }
-      pq += np;
-      const FlopTable &ft = flop_table();
-      const double fp = ft.prim[sp->h_cls[P]][sp->h_cls[Q]], fb = ft.bra[sp->h_cls[P]][sp->h_cls[Q]];
-      if (mixed && g * dm < sp->opts.fp32_cutoff) {
-        const double f = np * fp + nbra * fb + 12.0 * ne;
-        fl += f;
-        q32 += 1;
-        fl32 += f;
-      } else {
-        const double f32 = np32 * fp + nbra32 * fb;
-        fl += (np - np32) * fp + nbra64 * fb + 12.0 * ne + f32;
-        fl32 += f32;
+        acc[4] += np;
+        const double fp = ft.prim[sp->h_cls[P]][sp->h_cls[Q]], fb = ft.bra[sp->h_cls[P]][sp->h_cls[Q]];
+        if (mixed && g * dm < sp->opts.fp32_cutoff) {
+          const double f = np * fp + nbra * fb + 12.0 * ne;
+          acc[5] += f;
+          acc[6] += 1;
+          acc[7] += f;
+        } else {
+          const double f32 = np32 * fp + nbra32 * fb;
+          acc[5] += (np - np32) * fp + nbra64 * fb + 12.0 * ne + f32;
+          acc[7] += f32;
+        }
       }
     }
+  };
+  // every count is an integer below 2^53, so the per-thread partial sums add
+  // up exactly whatever the split
+  const size_t nu = sp->h_units.size();
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nthr = (int)std::max<size_t>(1, std::min<size_t>({(size_t)(hw ? hw : 1), (size_t)32, nu / 64 + 1}));
+  std::vector<std::array<double, 8>> part(nthr);
+  for (auto &a : part) a.fill(0.0);
+  {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthr; ++t)
+      pool.emplace_back([&, t] { count_units(nu * t / nthr, nu * (t + 1) / nthr, part[t].data()); });
+    for (auto &th : pool) th.join();
   }
+  double tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (const auto &a : part)
+    for (int k = 0; k < 8; ++k) tot[k] += a[k];
+  const double q1 = tot[0], e1 = tot[1], q2 = tot[2], e2 = tot[3], pq = tot[4], fl = tot[5], q32 = tot[6],
+               fl32 = tot[7];
   double nprim = 0;
   for (const int2 &p : sp->h_prim) nprim += p.y;
   out[0] = q1;

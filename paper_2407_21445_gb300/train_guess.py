@@ -146,8 +146,54 @@ def sensitivity(params: str, out: str, n: int = 500, ntrain: int = 400, nmol: in
     return summ
 
 
+def evaluate(params_npz: str, out: str, n: int = 500, ntrain: int = 400, limit: int = 0, seed: int = 0,
+             tau: float = 1e-10, log=print):
+    """Held-out comparison with a trained network and no retraining: per
+    held-out conformation the SCF from SAD and from the MLP guess, iterations
+    and wall time (guess construction, featurisation, network, projection and
+    SCF, the GPU synchronised) and the energy difference."""
+    os.makedirs(out, exist_ok=True)
+    table = molgen.basis_set("dz", seed)
+    mols = molgen.scf_conformations(n, seed)
+    _, test_idx = split(n, ntrain, seed)
+    if limit > 0:
+        test_idx = test_idx[:limit]
+    lg = G.LearnedGuess.load(params_npz)
+    sad_guess(mols[test_idx[0]], table)  # atomic densities cached outside the timings
+    res = []
+    for i in test_idx:
+        mol = mols[i]
+        basis = molgen.make_basis(mol, table)
+        out_i = {"natom": mol.natom}
+        for name in ("sad", "mlp"):
+            rhf = RHF(mol.Z.astype(float), mol.coords, basis, tau=tau)
+            torch.cuda.synchronize()
+            ts = time.time()
+            Ds = sad_guess(mol, table)
+            D0 = Ds if name == "sad" else lg.guess(mol, basis, rhf, Ds.cpu().numpy())
+            r = rhf.run(D0)
+            torch.cuda.synchronize()
+            out_i.update({f"{name}_t": time.time() - ts, f"{name}_it": r.iterations, f"{name}_E": r.energy,
+                          f"{name}_conv": r.converged})
+        out_i["dE"] = abs(out_i["mlp_E"] - out_i["sad_E"])
+        res.append(out_i)
+    rep = {"params": params_npz, "held_out": len(res),
+           "mean_iterations": {k: float(np.mean([r[f"{k}_it"] for r in res])) for k in ("sad", "mlp")},
+           "mean_wall_s": {k: float(np.mean([r[f"{k}_t"] for r in res])) for k in ("sad", "mlp")},
+           "max_abs_energy_diff_Eh": float(max(r["dE"] for r in res)),
+           "all_converged": bool(all(r["sad_conv"] and r["mlp_conv"] for r in res)), "per_molecule": res}
+    rep["iteration_reduction"] = 1.0 - rep["mean_iterations"]["mlp"] / rep["mean_iterations"]["sad"]
+    rep["wall_reduction"] = 1.0 - rep["mean_wall_s"]["mlp"] / rep["mean_wall_s"]["sad"]
+    with open(os.path.join(out, "evaluate.json"), "w") as f:
+        json.dump(rep, f, indent=1)
+    return rep
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--evaluate", default=None, metavar="PARAMS_NPZ",
+                    help="instead of training: held-out SCF iterations and wall time with a trained network")
+    ap.add_argument("--limit", type=int, default=0, help="--evaluate: first LIMIT held-out conformations (0 = all)")
     ap.add_argument("--sensitivity", default=None, metavar="PARAMS_NPZ",
                     help="instead of training: guess-accuracy study with a trained network")
     ap.add_argument("--n", type=int, default=500)
@@ -156,6 +202,10 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default="guess_run")
     a = ap.parse_args()
+    if a.evaluate:
+        rep = evaluate(a.evaluate, a.out, a.n, a.train, a.limit, seed=a.seed)
+        print(json.dumps({k: v for k, v in rep.items() if k != "per_molecule"}))
+        return
     if a.sensitivity:
         rep = sensitivity(a.sensitivity, a.out, a.n, a.train, seed=a.seed)
         print(json.dumps({k: v for k, v in rep.items() if k != "rows"}))
