@@ -15,6 +15,7 @@
 
 #include "fock_impl.h"
 #include "kernels_reg.cuh"
+#include "reg_dispatch.h"
 
 using namespace fk;
 
@@ -635,6 +636,12 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
         else
           t.reg = o.group_override == 0 && Ltot <= reg_max && avail;
       }
+      // mixed precision: the FP32 quartets of a total-L = 5 class pair run on
+      // its FP32 register kernel (k_reg32), so the pair gets group tiers of
+      // its own (its FP64 quartets stay on the group kernel)
+      if (!t.reg && !o.tune_isolate && o.group_override == 0 && o.precision == FOCK_MIXED && o.fp32_cutoff > 0.0 &&
+          reg32_class_pair(bins[t.bra].cls, bins[t.ket].cls))
+        t.tag = kReg32Tag + bins[t.bra].cls * FOCK_NCLASS + bins[t.ket].cls;
       tasks.push_back(t);
     }
   std::stable_sort(tasks.begin(), tasks.end(), [](const Task &a, const Task &b) { return a.cost > b.cost; });
@@ -676,6 +683,10 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
     tier.sb = keys[ki].sb;
     tier.tag = keys[ki].tag;
     tier.mixed = (o.precision == FOCK_MIXED && o.fp32_cutoff > 0.0) ? 1 : 0;
+    if (tier.tag >= kReg32Tag) {
+      tier.r32_cb = (tier.tag - kReg32Tag) / FOCK_NCLASS;
+      tier.r32_ck = (tier.tag - kReg32Tag) % FOCK_NCLASS;
+    }
     int stride = 1;
     const int chunk = (32 / tier.G) * 8;
     const size_t first = all_units.size();

@@ -138,12 +138,18 @@ struct Unit {
   int bra, k0, k1, pad;
 };
 
+// Tier tags at or above this mark the per-class-pair group tiers of the
+// FP32 register kernels (tag - kReg32Tag = bra class * NCLASS + ket class).
+constexpr int kReg32Tag = 1000;
+
 struct Tier {
   int reg_cb = -1;      // >= 0: per-class register kernel for (bra class, ket class)
   int reg_ck = -1;
   int sb = 0;           // scratch bucket of a full-warp group tier
   int tag = 0;          // class pair + 1 when class pairs are launched apart (tuning)
   int mixed = 0;        // 1: mixed-precision build (kernel variant with FP32 paths)
+  int r32_cb = -1;      // >= 0: a group tier of one class pair whose FP32 part
+  int r32_ck = -1;      //   runs on the FP32 register kernel k_reg32<cb, ck>
   int G;                // lanes per quartet (group kernel)
   int stride;           // scratch doubles per group
   int warps_per_block;

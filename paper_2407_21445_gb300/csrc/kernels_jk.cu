@@ -971,6 +971,7 @@ static cudaError_t launch_g(const Tier &t, KArgs a, int threads, cudaStream_t st
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     a.counter = counter2;
+    if (t.r32_cb >= 0) return launch_reg32(t.r32_cb, t.r32_ck, a, t.blocks32, 128, st);
     a.stride = fp32_stride(t.stride);  // scratch counted in doubles, half of them needed
     k_jk<G, 2><<<t.blocks32 > 0 ? t.blocks32 : t.blocks, threads, t.smem32 > 0 ? t.smem32 : t.smem, st>>>(a);
   } else {
@@ -1014,14 +1015,22 @@ static cudaError_t configure_g(Tier &t) {
   t.blocks = nsm * per_sm;
   const int need = (t.nunits + wpb - 1) / wpb;
   if (t.blocks > need) t.blocks = need > 0 ? need : 1;
-  // FP32 part of a mixed tier: same warps per block, half the scratch
-  t.smem32 = TAB_BYTES + wpb * per_warp32;
+  // FP32 part of a mixed tier: same warps per block, half the scratch; or
+  // the class pair's FP32 register kernel (four warps per block)
   int per_sm32 = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_jk<G, 2>, 32 * wpb, t.smem32);
+  int need32 = need;
+  if (t.r32_cb >= 0) {
+    t.smem32 = 0;
+    e = occupancy_reg32(t.r32_cb, t.r32_ck, 128, &per_sm32);
+    need32 = (t.nunits + 3) / 4;
+  } else {
+    t.smem32 = TAB_BYTES + wpb * per_warp32;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_jk<G, 2>, 32 * wpb, t.smem32);
+  }
   if (e != cudaSuccess) return e;
   if (per_sm32 < 1) per_sm32 = 1;
   t.blocks32 = nsm * per_sm32;
-  if (t.blocks32 > need) t.blocks32 = need > 0 ? need : 1;
+  if (t.blocks32 > need32) t.blocks32 = need32 > 0 ? need32 : 1;
   return cudaSuccess;
 }
 

@@ -346,13 +346,25 @@ __device__ __forceinline__ void quartet_reg_f64(const KArgs &a, const MolView &m
 // recursion, transforms and digestion; centres are taken relative to the
 // pair's first shell so that P - Q keeps its precision; each digested J/K
 // element is converted exactly to FP64 and accumulated in FP64.
+// Classes with total L >= 5 (FP32 quartets only, k_reg32) keep the FP32
+// contracted-ERI accumulator in per-thread shared memory, [element][thread].
+template <int LA, int LB, int LC, int LD>
+__host__ __device__ constexpr bool reg32_eri_in_smem() {
+  return LA + LB + LC + LD >= 5;
+}
+template <int LA, int LB, int LC, int LD>
+__host__ __device__ constexpr int reg32_smem_bytes(int threads) {
+  return reg32_eri_in_smem<LA, LB, LC, LD>() ? ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD) * threads * 4 : 0;
+}
+
 template <int LA, int LB, int LC, int LD>
 __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &mv, int P, int Q, int sA, int sB,
-                                                int sC, int sD) {
+                                                int sC, int sD, float *eri_col = nullptr) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
   constexpr int NAB = NA * NB, NCD = NC * ND;
   constexpr int LAB = LA + LB, L = LA + LB + LC + LD;
   constexpr int NHAB = nherm(LAB), NHL = nherm(L);
+  constexpr bool SM = reg32_eri_in_smem<LA, LB, LC, LD>();
   const DevPairs &dp = a.dp;
   // A - C from hi/lo FP32 parts: the hi difference rounds once relative to
   // |A - C| itself, the lo parts restore the bits the hi parts dropped
@@ -360,8 +372,15 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
   const float ACx = (ha[0] - hc[0]) + (ha[3] - hc[3]);
   const float ACy = (ha[1] - hc[1]) + (ha[4] - hc[4]);
   const float ACz = (ha[2] - hc[2]) + (ha[5] - hc[5]);
-  float eri[NAB * NCD];
-  sfor<NAB * NCD>([&](auto i) { eri[FK_CI(i)] = 0.0f; });
+  float eri_r[SM ? 1 : NAB * NCD];
+  const int bs = blockDim.x;
+  auto eri = [&](int i) -> float & {
+    if constexpr (SM)
+      return eri_col[i * bs];
+    else
+      return eri_r[i];
+  };
+  sfor<NAB * NCD>([&](auto i) { eri(FK_CI(i)) = 0.0f; });
   const int2 pb = dp.prim[P], pk = dp.prim[Q];
   const PrimScreen ps = prim_screen(a, mv, sA, sB, sC, sD);
   for (int ip = pb.x; ip < pb.x + pb.y; ++ip) {
@@ -411,7 +430,7 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
         const float ev = __ldg(EP + e0 + qq);
         sfor<NCD>([&](auto kci) {
           constexpr int kc = FK_CI(kci);
-          eri[ka * NCD + kc] = fmaf(ev, Y[ct_hidx(t, u, v) * NCD + kc], eri[ka * NCD + kc]);
+          eri(ka * NCD + kc) = fmaf(ev, Y[ct_hidx(t, u, v) * NCD + kc], eri(ka * NCD + kc));
         });
       });
     });
@@ -426,7 +445,7 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
   const float *__restrict__ Dm = mv.Df;
   double *__restrict__ Jm = mv.J;
   double *__restrict__ Km = mv.K;
-  auto E4 = [&](int ia, int ib, int ic, int id) -> float { return eri[(ia * NB + ib) * NCD + ic * ND + id]; };
+  auto E4 = [&](int ia, int ib, int ic, int id) -> float { return eri((ia * NB + ib) * NCD + ic * ND + id); };
   auto Dv = [&](int r, int c) -> float { return __ldg(Dm + (size_t)r * N + c); };
   if (a.parts & 1) {
   sfor<NAB>([&](auto k) {
@@ -558,6 +577,68 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
   }
   drain_reg<LA, LB, LC, LD, MIXED>(a, p64, q64, n64, false, eri_col, lane);
   if constexpr (MIXED) drain_reg<LA, LB, LC, LD, MIXED>(a, p32, q32, n32, true, eri_col, lane);
+}
+
+// FP32 quartets of a class pair with total L = 5 (the FP32 part of a mixed
+// group tier; its FP64 quartets run on the group kernel): one thread per
+// quartet with compile-time loops, the FP32 ERI accumulator in per-thread
+// shared memory.  Same warp queue as k_reg, FP32 quartets only.
+template <int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(128) k_reg32(KArgs a) {
+  extern __shared__ __align__(16) float reg32_smem[];
+  __shared__ int queues[4][2][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float *eri_col = reg32_smem + threadIdx.x;
+  int *qp = queues[warp][0], *qq = queues[warp][1];
+  const unsigned lt = (1u << lane) - 1u;
+  auto drain = [&](int n) {
+    if (lane < n) {
+      const int P = qp[lane], Q = qq[lane];
+      const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
+      const MolView mv = mol_view(a, ab.x);
+      quartet_reg_f32<LA, LB, LC, LD>(a, mv, P, Q, ab.x, ab.y, cd.x, cd.y, eri_col);
+    }
+  };
+  int n32 = 0;
+  for (;;) {
+    const int u = next_unit(a.counter, lane);
+    if (u >= a.nunits) break;
+    const Unit un = a.units[u];
+    const int P = un.bra;
+    const int2 ab = a.dp.ab[P];
+    const MolView mv = mol_view(a, ab.x);
+    for (int c = un.k0; c < un.k1; c += 32) {
+      const int Q = c + lane;
+      float b = -1.0f;
+      if (Q < un.k1) {
+        const int2 cd = a.dp.ab[Q];
+        b = quartet_bound(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
+      }
+      const bool is32 = b >= 0.0f && b < a.fp32_cutoff_f;
+      const unsigned m32 = __ballot_sync(0xffffffffu, is32);
+      if (is32) {
+        const int k = n32 + __popc(m32 & lt);
+        qp[k] = P;
+        qq[k] = Q;
+      }
+      n32 += __popc(m32);
+      __syncwarp();
+      if (n32 >= 32) {
+        drain(32);
+        __syncwarp();
+        const bool mv_ = lane + 32 < n32;
+        const int rp = mv_ ? qp[lane + 32] : 0, rq = mv_ ? qq[lane + 32] : 0;
+        __syncwarp();
+        if (mv_) {
+          qp[lane] = rp;
+          qq[lane] = rq;
+        }
+        n32 -= 32;
+        __syncwarp();
+      }
+    }
+  }
+  drain(n32);
 }
 
 // (bra class, ket class) pairs served by register kernels: total L <= 4

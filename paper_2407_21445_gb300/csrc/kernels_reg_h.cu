@@ -1,0 +1,48 @@
+// FP32-only register kernels (k_reg32) of the f-shell class pairs with total L = 5.
+#include "kernels_reg.cuh"
+#include "reg_dispatch.h"
+
+namespace fk {
+
+#define FK_REG32_LIST(X) \
+  X(6, 2, 3, 0, 1, 1) \
+  X(2, 6, 1, 1, 3, 0) \
+  X(6, 3, 3, 0, 2, 0) \
+  X(3, 6, 2, 0, 3, 0) \
+  X(7, 1, 3, 1, 1, 0) \
+  X(1, 7, 1, 0, 3, 1) \
+  X(8, 0, 3, 2, 0, 0) \
+  X(0, 8, 0, 0, 3, 2)
+
+cudaError_t launch_reg32_h(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st) {
+#define FK_R32_LAUNCH(CB, CK, LA, LB, LC, LD)                                                           \
+  if (cb == CB && ck == CK) {                                                                            \
+    const int sm = reg32_smem_bytes<LA, LB, LC, LD>(threads);                                           \
+    if (sm > 48 * 1024) {                                                                                \
+      cudaError_t e = cudaFuncSetAttribute(k_reg32<LA, LB, LC, LD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); \
+      if (e != cudaSuccess) return e;                                                                    \
+    }                                                                                                    \
+    k_reg32<LA, LB, LC, LD><<<blocks, threads, sm, st>>>(a);                                             \
+    return cudaGetLastError();                                                                           \
+  }
+  FK_REG32_LIST(FK_R32_LAUNCH)
+#undef FK_R32_LAUNCH
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t occupancy_reg32_h(int cb, int ck, int threads, int *per_sm) {
+#define FK_R32_OCC(CB, CK, LA, LB, LC, LD)                                                              \
+  if (cb == CB && ck == CK) {                                                                            \
+    const int sm = reg32_smem_bytes<LA, LB, LC, LD>(threads);                                           \
+    if (sm > 48 * 1024) {                                                                                \
+      cudaError_t e = cudaFuncSetAttribute(k_reg32<LA, LB, LC, LD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); \
+      if (e != cudaSuccess) return e;                                                                    \
+    }                                                                                                    \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_reg32<LA, LB, LC, LD>, threads, sm);    \
+  }
+  FK_REG32_LIST(FK_R32_OCC)
+#undef FK_R32_OCC
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace fk

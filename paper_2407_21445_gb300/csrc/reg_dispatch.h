@@ -17,6 +17,28 @@ cudaError_t occupancy_reg_e(int cb, int ck, int threads, bool mixed, int *per_sm
 cudaError_t launch_reg_f(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st);
 cudaError_t occupancy_reg_f(int cb, int ck, int threads, bool mixed, int *per_sm);
 
+cudaError_t launch_reg32_g(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st);
+cudaError_t occupancy_reg32_g(int cb, int ck, int threads, int *per_sm);
+cudaError_t launch_reg32_h(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st);
+cudaError_t occupancy_reg32_h(int cb, int ck, int threads, int *per_sm);
+
+// Class pairs (bra class, ket class) with an FP32-only register kernel
+// (k_reg32): total angular momentum 5, l <= 3.
+__host__ __device__ constexpr bool reg32_class_pair(int cb, int ck) {
+  constexpr int Lc[NCLASS] = {0, 1, 2, 2, 3, 4, 3, 4, 5, 6};
+  return cb >= 0 && ck >= 0 && cb < NCLASS && ck < NCLASS && Lc[cb] + Lc[ck] == 5;
+}
+inline cudaError_t launch_reg32(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st) {
+  cudaError_t e = launch_reg32_g(cb, ck, a, blocks, threads, st);
+  if (e == cudaErrorInvalidValue) e = launch_reg32_h(cb, ck, a, blocks, threads, st);
+  return e;
+}
+inline cudaError_t occupancy_reg32(int cb, int ck, int threads, int *per_sm) {
+  cudaError_t e = occupancy_reg32_g(cb, ck, threads, per_sm);
+  if (e == cudaErrorInvalidValue) e = occupancy_reg32_h(cb, ck, threads, per_sm);
+  return e;
+}
+
 // Launch / occupancy of the register kernel of class pair (cb, ck), whichever
 // translation unit instantiates it (cudaErrorInvalidValue if none does).
 inline cudaError_t launch_reg(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st) {
