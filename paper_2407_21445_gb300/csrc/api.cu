@@ -640,7 +640,7 @@ fock_status fock_shellpairs_build(const fock_basis_desc *desc, const fock_opts *
       // its FP32 register kernel (k_reg32), so the pair gets group tiers of
       // its own (its FP64 quartets stay on the group kernel)
       if (!t.reg && !o.tune_isolate && o.group_override == 0 && o.precision == FOCK_MIXED && o.fp32_cutoff > 0.0 &&
-          reg32_class_pair(bins[t.bra].cls, bins[t.ket].cls))
+          reg32_available(bins[t.bra].cls, bins[t.ket].cls))
         t.tag = kReg32Tag + bins[t.bra].cls * FOCK_NCLASS + bins[t.ket].cls;
       tasks.push_back(t);
     }

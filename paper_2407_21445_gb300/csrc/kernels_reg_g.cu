@@ -1,4 +1,5 @@
-// FP32-only register kernels (k_reg32) of the d-shell class pairs with total L = 5.
+// FP32-only register kernels (k_reg32) of the d-shell class pairs with total L = 5
+// and of (dd|pp).
 #include "kernels_reg.cuh"
 #include "reg_dispatch.h"
 
@@ -10,7 +11,16 @@ namespace fk {
   X(4, 2, 2, 1, 1, 1) \
   X(2, 4, 1, 1, 2, 1) \
   X(4, 3, 2, 1, 2, 0) \
-  X(3, 4, 2, 0, 2, 1)
+  X(3, 4, 2, 0, 2, 1) \
+  X(5, 2, 2, 2, 1, 1)
+
+bool reg32_listed_g(int cb, int ck) {
+#define FK_R32_HAS(CB, CK, LA, LB, LC, LD) \
+  if (cb == CB && ck == CK) return true;
+  FK_REG32_LIST(FK_R32_HAS)
+#undef FK_R32_HAS
+  return false;
+}
 
 cudaError_t launch_reg32_g(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st) {
 #define FK_R32_LAUNCH(CB, CK, LA, LB, LC, LD)                                                           \

@@ -14,6 +14,14 @@ namespace fk {
   X(8, 0, 3, 2, 0, 0) \
   X(0, 8, 0, 0, 3, 2)
 
+bool reg32_listed_h(int cb, int ck) {
+#define FK_R32_HAS(CB, CK, LA, LB, LC, LD) \
+  if (cb == CB && ck == CK) return true;
+  FK_REG32_LIST(FK_R32_HAS)
+#undef FK_R32_HAS
+  return false;
+}
+
 cudaError_t launch_reg32_h(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st) {
 #define FK_R32_LAUNCH(CB, CK, LA, LB, LC, LD)                                                           \
   if (cb == CB && ck == CK) {                                                                            \

@@ -22,12 +22,12 @@ cudaError_t occupancy_reg32_g(int cb, int ck, int threads, int *per_sm);
 cudaError_t launch_reg32_h(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st);
 cudaError_t occupancy_reg32_h(int cb, int ck, int threads, int *per_sm);
 
+bool reg32_listed_g(int cb, int ck);
+bool reg32_listed_h(int cb, int ck);
 // Class pairs (bra class, ket class) with an FP32-only register kernel
-// (k_reg32): total angular momentum 5, l <= 3.
-__host__ __device__ constexpr bool reg32_class_pair(int cb, int ck) {
-  constexpr int Lc[NCLASS] = {0, 1, 2, 2, 3, 4, 3, 4, 5, 6};
-  return cb >= 0 && ck >= 0 && cb < NCLASS && ck < NCLASS && Lc[cb] + Lc[ck] == 5;
-}
+// (k_reg32), as instantiated: total angular momentum 5 (l <= 3) and (dd|pp)
+// (the other total-6 pairs would spill kilobytes per thread).
+inline bool reg32_available(int cb, int ck) { return reg32_listed_g(cb, ck) || reg32_listed_h(cb, ck); }
 inline cudaError_t launch_reg32(int cb, int ck, const KArgs &a, int blocks, int threads, cudaStream_t st) {
   cudaError_t e = launch_reg32_g(cb, ck, a, blocks, threads, st);
   if (e == cudaErrorInvalidValue) e = launch_reg32_h(cb, ck, a, blocks, threads, st);
