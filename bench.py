@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the c20h42 and batched extra keys")
     ap.add_argument("--k-thresh", type=float, default=5e-6, help="tau* of the decay-bound exchange mode")
     ap.add_argument("--batched-nmol", type=int, default=32, help="molecules of the batched extra key")
+    ap.add_argument("--mma-peak", action="store_true",
+                    help="measure the mma.sync tensor-core rates (f64, tf32, bf16, s8) on one GPU and exit")
     ap.add_argument("--fma-peak", action="store_true",
                     help="measure the DFMA and FFMA peaks with a register-only FMA probe (built with nvcc) and exit")
     ap.add_argument("--chain-study", default=None, metavar="N1,N2,...",
@@ -504,22 +506,123 @@ void run(int blocks, int threads, int iters) {
          sizeof(T) == 8 ? "DFMA" : "FFMA", blocks, threads, NCH, iters, ms / reps, flops / (ms * 1e-3) / 1e12,
          cudaGetErrorString(err));
 }
-int main() {
+// mma.sync probes: every warp runs NCH independent accumulator chains of
+// one tensor-core shape (KIND 0: f64 m8n8k4, 1: tf32 m16n8k8 with f32
+// accumulation, 2: bf16 m16n8k16 with f32 accumulation, 3: s8 m16n8k32 with
+// s32 accumulation), operands in registers.
+template <int KIND, int NCH>
+__global__ void k_mma(float *out, int iters) {
+  const unsigned t = threadIdx.x;
+  float s = 0.f;
+  if constexpr (KIND == 0) {
+    const double a = 1.0 + t * 1e-3, b = 0.5 - t * 1e-4;
+    double c[NCH][2];
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) c[i][0] = c[i][1] = (double)i;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < NCH; ++i)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                     : "+d"(c[i][0]), "+d"(c[i][1]) : "d"(a), "d"(b));
+    }
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) s += (float)(c[i][0] + c[i][1]);
+  } else if constexpr (KIND == 1 || KIND == 2) {
+    const unsigned a0 = 0x3f800000u ^ (t << 4), a1 = 0x3f000000u ^ (t << 5), b0 = 0x3e800000u ^ (t << 6),
+                   b1 = 0x3f400000u ^ (t << 3);
+    float c[NCH][4];
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) c[i][0] = c[i][1] = c[i][2] = c[i][3] = (float)i;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < NCH; ++i) {
+        if constexpr (KIND == 1)
+          asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                       "{%8, %9}, {%0, %1, %2, %3};"
+                       : "+f"(c[i][0]), "+f"(c[i][1]), "+f"(c[i][2]), "+f"(c[i][3])
+                       : "r"(a0), "r"(a1), "r"(a1), "r"(a0), "r"(b0), "r"(b1));
+        else
+          asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                       "{%8, %9}, {%0, %1, %2, %3};"
+                       : "+f"(c[i][0]), "+f"(c[i][1]), "+f"(c[i][2]), "+f"(c[i][3])
+                       : "r"(a0), "r"(a1), "r"(a1), "r"(a0), "r"(b0), "r"(b1));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) s += c[i][0] + c[i][1] + c[i][2] + c[i][3];
+  } else {
+    const unsigned a0 = 0x01020304u ^ t, a1 = 0x05060708u ^ (t << 8), b0 = 0x0a0b0c0du ^ (t << 16),
+                   b1 = 0x01010101u ^ t;
+    int c[NCH][4];
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) c[i][0] = c[i][1] = c[i][2] = c[i][3] = i;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < NCH; ++i)
+        asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                     "{%8, %9}, {%0, %1, %2, %3};"
+                     : "+r"(c[i][0]), "+r"(c[i][1]), "+r"(c[i][2]), "+r"(c[i][3])
+                     : "r"(a0), "r"(a1), "r"(a1), "r"(a0), "r"(b0), "r"(b1));
+    }
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) s += (float)(c[i][0] ^ c[i][1] ^ c[i][2] ^ c[i][3]);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+template <int KIND, int NCH>
+void run_mma(int blocks, int threads, int iters) {
+  static const char *names[4] = {"DMMA f64 m8n8k4", "mma tf32 m16n8k8", "mma bf16 m16n8k16", "mma s8 m16n8k32"};
+  static const double ops[4] = {2.0 * 8 * 8 * 4, 2.0 * 16 * 8 * 8, 2.0 * 16 * 8 * 16, 2.0 * 16 * 8 * 32};
+  float *d = nullptr;
+  if (cudaMalloc(&d, sizeof(float) * blocks * threads) != cudaSuccess) return;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int w = 0; w < 3; ++w) k_mma<KIND, NCH><<<blocks, threads>>>(d, iters);
+  const int reps = 5;
+  cudaEventRecord(e0);
+  for (int r = 0; r < reps; ++r) k_mma<KIND, NCH><<<blocks, threads>>>(d, iters);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaError_t err = cudaGetLastError();
+  cudaFree(d);
+  const double warps = (double)blocks * threads / 32;
+  const double flops = ops[KIND] * NCH * (double)iters * warps * reps;
+  printf("{\"pipe\": \"%s\", \"blocks\": %d, \"threads\": %d, \"chains\": %d, \"iters\": %d, "
+         "\"ms_per_launch\": %.4f, \"tflops\": %.4f, \"status\": \"%s\"}\n",
+         names[KIND], blocks, threads, NCH, iters, ms / reps, flops / (ms * 1e-3) / 1e12, cudaGetErrorString(err));
+}
+int main(int argc, char **argv) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  run<double, 8>(sms * 8, 256, 20000);
-  run<double, 8>(sms * 4, 256, 40000);
-  run<double, 16>(sms * 8, 256, 10000);
-  run<float, 8>(sms * 8, 256, 400000);
-  run<float, 16>(sms * 8, 256, 200000);
-  run<float, 8>(sms * 16, 256, 200000);
+  const bool mma = argc > 1 && argv[1][0] == 'm';
+  if (!mma) {
+    run<double, 8>(sms * 8, 256, 20000);
+    run<double, 8>(sms * 4, 256, 40000);
+    run<double, 16>(sms * 8, 256, 10000);
+    run<float, 8>(sms * 8, 256, 400000);
+    run<float, 16>(sms * 8, 256, 200000);
+    run<float, 8>(sms * 16, 256, 200000);
+    return 0;
+  }
+  run_mma<0, 8>(sms * 8, 128, 4000);
+  run_mma<0, 4>(sms * 16, 128, 4000);
+  run_mma<1, 8>(sms * 8, 128, 40000);
+  run_mma<1, 4>(sms * 16, 128, 40000);
+  run_mma<2, 8>(sms * 8, 128, 40000);
+  run_mma<2, 4>(sms * 16, 128, 40000);
+  run_mma<3, 8>(sms * 8, 128, 20000);
+  run_mma<3, 4>(sms * 16, 128, 20000);
   return 0;
 }
 """
 
 
-def fma_peak():
-    """Build and run the FMA probe (sm_103a) with nvidia-smi clocks sampled."""
+def fma_peak(which="fma"):
+    """Build and run the pipe probe (sm_103a) with nvidia-smi clocks sampled:
+    which = "fma" (DFMA / FFMA) or "mma" (mma.sync f64 / tf32 / bf16 / s8)."""
     import shutil
     out_dir = os.path.join(ROOT, "paper_2407_21445_gb300", "_build")
     os.makedirs(out_dir, exist_ok=True)
@@ -529,7 +632,7 @@ def fma_peak():
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
     with ClockSampler(0) as clk:
-        r = subprocess.run([exe], capture_output=True, text=True, check=True)
+        r = subprocess.run([exe, which], capture_output=True, text=True, check=True)
     for line in r.stdout.splitlines():
         print(line)
     print(json.dumps({"clocks": clk.summary()}))
@@ -580,6 +683,8 @@ def main():
         return run_reference(args, rank, world)
     if args.fma_peak:
         return fma_peak()
+    if args.mma_peak:
+        return fma_peak("mma")
 
     import torch
 

@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "device_common.cuh"
 #include "kargs.cuh"
@@ -953,11 +954,26 @@ cudaError_t launch_symmetrize(double *J, double *K, int n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The dynamic shared-memory limit of the group kernels is raised, never
+// lowered (per device, to the largest size any tier has asked for): a CUDA
+// graph's kernel nodes keep the sizes of the tiers they were captured from,
+// and a node launched on its own (as a profiler replaying a graph node by node
+// does) is checked against the function's current limit.  The call is repeated
+// every time, so a limit lost with the context (cudaDeviceReset) comes back.
 template <int G>
 static cudaError_t set_smem_g(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_jk<G, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_jk<G, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_jk<G, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::mutex mu;
+  static int raised[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool tracked = dev >= 0 && dev < 64;
+  std::lock_guard<std::mutex> lock(mu);
+  const int target = std::max((int)smem, tracked ? raised[dev] : 0);
+  e = cudaFuncSetAttribute(k_jk<G, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, target);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_jk<G, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, target);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_jk<G, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, target);
+  if (e == cudaSuccess && tracked) raised[dev] = target;
   return e;
 }
 
@@ -1062,7 +1078,7 @@ cudaError_t configure_tier(Tier &t) {
 }
 
 // The dynamic shared-memory limit is a per-function attribute shared by
-// every handle; raise it to this tier's need before launching.
+// every handle; make sure it covers this tier's need before launching.
 static cudaError_t set_group_smem(const Tier &t) {
   switch (t.G) {
     case 1: return set_smem_g<1>(t.smem);
