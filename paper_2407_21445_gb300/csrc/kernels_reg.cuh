@@ -488,9 +488,6 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
   });
 }
 
-// One quartet: screening, then the FP32 path below the mixed-precision
-// cutoff (0 in the FP64 mode) or the FP64 path.
-
 // Warp-level work queue: a unit's kets are screened 32 at a time and the
 // surviving (bra, ket) pairs appended to an FP64 or an FP32 queue (ballot +
 // prefix popcount); each full queue is drained 32 quartets at a time, so every
@@ -498,62 +495,72 @@ __device__ __forceinline__ void quartet_reg_f32(const KArgs &a, const MolView &m
 // no lane time.  The queues carry over from one unit to the next (all units
 // of a launch are of one class pair), so a warp leaves a partly filled batch
 // only once, after its last unit.
-template <int LA, int LB, int LC, int LD, bool MIXED>
-__device__ __forceinline__ void drain_reg(const KArgs &a, const int *qp, const int *qq, int n, bool fp32,
-                                          double *eri_col, int lane) {
-  if (lane < n) {
+template <int LA, int LB, int LC, int LD, bool MIXED, bool F32>
+__device__ __forceinline__ void drain_reg(const KArgs &a, int *qp, int *qq, int &n, double *eri_col, int lane) {
+  const int m = n < 32 ? n : 32;
+  if (lane < m) {
     const int P = qp[lane], Q = qq[lane];
     const int2 ab = a.dp.ab[P], cd = a.dp.ab[Q];
     const MolView mv = mol_view(a, ab.x);
-    if (MIXED && fp32)
+    if constexpr (F32)
       quartet_reg_f32<LA, LB, LC, LD>(a, mv, P, Q, ab.x, ab.y, cd.x, cd.y);
     else
       quartet_reg_f64<LA, LB, LC, LD, MIXED>(a, mv, P, Q, ab.x, ab.y, cd.x, cd.y, eri_col);
   }
+  __syncwarp();
+  // move the rest (< 32 entries) forward
+  const bool mv_ = lane + 32 < n;
+  const int rp = mv_ ? qp[lane + 32] : 0, rq = mv_ ? qq[lane + 32] : 0;
+  __syncwarp();
+  if (mv_) {
+    qp[lane] = rp;
+    qq[lane] = rq;
+  }
+  n -= m;
+  __syncwarp();
 }
 
 // MIXED = false: the lean FP64 fused J+K build (no FP32 code, exact test
 // only); true: every feature -- mixed precision (FP32 quartets below the
 // cutoff, FP32 primitive tails above it), J-only / K-only builds and the
-// decay-bound exchange test.
+// decay-bound exchange test.  One loop screens a 32-ket chunk per pass and
+// drains whichever queue holds a full batch (every queue at the end), so
+// each quartet body is inlined once.
 template <int LA, int LB, int LC, int LD, bool MIXED>
 __global__ void __launch_bounds__(128) k_reg(KArgs a) {
   extern __shared__ __align__(16) double reg_smem[];
-  __shared__ int queues[4][2][2][64];  // per warp: FP64 / FP32 queue of (bra, ket)
+  constexpr int NQ = MIXED ? 2 : 1;  // FP64 queue, FP32 queue
+  __shared__ int queues[4][NQ][2][64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double *eri_col = reg_smem + threadIdx.x;
   int *p64 = queues[warp][0][0], *q64 = queues[warp][0][1];
-  int *p32 = queues[warp][1][0], *q32 = queues[warp][1][1];
+  int *p32 = queues[warp][NQ - 1][0], *q32 = queues[warp][NQ - 1][1];
   const unsigned lt = (1u << lane) - 1u;
-  // drain the first 32 entries of a queue and move the rest (< 32) forward
-  auto drain32 = [&](int *qp, int *qq, int &n, bool fp32) {
-    drain_reg<LA, LB, LC, LD, MIXED>(a, qp, qq, 32, fp32, eri_col, lane);
-    __syncwarp();
-    const bool mv_ = lane + 32 < n;
-    const int rp = mv_ ? qp[lane + 32] : 0, rq = mv_ ? qq[lane + 32] : 0;
-    __syncwarp();
-    if (mv_) {
-      qp[lane] = rp;
-      qq[lane] = rq;
-    }
-    n -= 32;
-    __syncwarp();
-  };
   int n64 = 0, n32 = 0;
+  bool more = true;  // units left to screen
+  int P = 0, c = 0, k1 = 0;
   for (;;) {
-    const int u = next_unit(a.counter, lane);
-    if (u >= a.nunits) break;
-    const Unit un = a.units[u];
-    const int P = un.bra;
-    const int2 ab = a.dp.ab[P];
-    const MolView mv = mol_view(a, ab.x);
-    for (int c = un.k0; c < un.k1; c += 32) {
+    if (more && c >= k1) {
+      const int u = next_unit(a.counter, lane);
+      if (u < a.nunits) {
+        const Unit un = a.units[u];
+        P = un.bra;
+        c = un.k0;
+        k1 = un.k1;
+      } else {
+        more = false;
+      }
+    }
+    if (more) {
+      const int2 ab = a.dp.ab[P];
       const int Q = c + lane;
       float b = -1.0f;
-      if (Q < un.k1) {
+      if (Q < k1) {
+        const MolView mv = mol_view(a, ab.x);
         const int2 cd = a.dp.ab[Q];
         b = quartet_bound<MIXED>(a, mv, ab.x, ab.y, cd.x, cd.y, P, Q);
       }
+      c += 32;
       const bool is32 = MIXED && b >= 0.0f && b < a.fp32_cutoff_f, is64 = b >= 0.0f && !is32;
       const unsigned m64 = __ballot_sync(0xffffffffu, is64), m32 = __ballot_sync(0xffffffffu, is32);
       if (is64) {
@@ -569,14 +576,13 @@ __global__ void __launch_bounds__(128) k_reg(KArgs a) {
       n64 += __popc(m64);
       n32 += __popc(m32);
       __syncwarp();
-      if (n64 >= 32) drain32(p64, q64, n64, false);
-      if constexpr (MIXED) {
-        if (n32 >= 32) drain32(p32, q32, n32, true);
-      }
     }
+    if (n64 >= 32 || (!more && n64 > 0)) drain_reg<LA, LB, LC, LD, MIXED, false>(a, p64, q64, n64, eri_col, lane);
+    if constexpr (MIXED) {
+      if (n32 >= 32 || (!more && n32 > 0)) drain_reg<LA, LB, LC, LD, MIXED, true>(a, p32, q32, n32, eri_col, lane);
+    }
+    if (!more && n64 == 0 && n32 == 0) break;
   }
-  drain_reg<LA, LB, LC, LD, MIXED>(a, p64, q64, n64, false, eri_col, lane);
-  if constexpr (MIXED) drain_reg<LA, LB, LC, LD, MIXED>(a, p32, q32, n32, true, eri_col, lane);
 }
 
 // FP32 quartets of a class pair with total L = 5 (the FP32 part of a mixed
