@@ -35,8 +35,9 @@ def test_mixed_peak_fraction_arithmetic():
 
 
 def test_fma_probe_compiles_for_sm103a(tmp_path):
-    """The probe behind the FP64/FP32 peak figures (bench.py --fma-peak)
-    compiles for sm_103a (it runs only on a GPU)."""
+    """The probe behind the FP64/FP32 peak figures and the mma.sync rates
+    (bench.py --fma-peak / --mma-peak) compiles for sm_103a (it runs only on
+    a GPU) and holds the four tensor-core shapes it reports."""
     import shutil
     import bench
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
@@ -45,3 +46,6 @@ def test_fma_probe_compiles_for_sm103a(tmp_path):
     out = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-c", str(src), "-o",
                           str(tmp_path / "probe.o")], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
+    for shape in ("m8n8k4.row.col.f64", "m16n8k8.row.col.f32.tf32", "m16n8k16.row.col.f32.bf16",
+                  "m16n8k32.row.col.s32.s8"):
+        assert shape in bench.FMA_PROBE_SRC
