@@ -322,84 +322,174 @@ __device__ void quartet_body(const KArgs &a, const ClassTables &ct, double *scr_
   const Real fac2 = Real(2) * fac;
   const int n1 = nab, n2 = n1 + ncd, n3 = n2 + na * nc, n4 = n3 + na * nd, n5 = n4 + nb * nc,
             n6 = n5 + nb * nd;
-  // The six density sub-blocks D_ab, D_cd, D_ac, D_ad, D_bc, D_bd, each a
-  // row-major block with row stride ldb: staged once in the scratch the
-  // transforms no longer need (Yh, R0, R1, F) when they fit there, else read
-  // from D in place (row stride N).
-  const Real *Db[6];
-  int ldb[6];
-  const int r0[6] = {fa, fc, fa, fa, fb, fb}, c0[6] = {fb, fd, fc, fd, fc, fd};
-  const int nr[6] = {na, nc, na, na, nb, nb}, ncl[6] = {nb, nd, nc, nd, nc, nd};
-  const int nstage = nab + ncd + (na + nb) * (nc + nd);
-  if (nstage <= nhab * ncd + 2 * nhL + L + 1) {
-    Real *Ds = Yh;
-    int off = 0;
-    for (int k = 0; k < 6; ++k) {
-      Db[k] = Ds + off;
-      ldb[k] = ncl[k];
-      const int nk = nr[k] * ncl[k];
-      for (int i = gl; i < nk; i += G) {
-        const int r = i / ncl[k], c = i - r * ncl[k];
-        Ds[off + i] = Dm[(size_t)(r0[k] + r) * N + c0[k] + c];
+  // FP32 bodies and groups of up to 8 lanes stage the density sub-blocks;
+  // the FP64 bodies of 16- and 32-lane groups read D in place, which
+  // measured faster there (the staging round trip is not repaid by the
+  // few outputs per lane).
+  constexpr bool kStage = F32 || G <= 8;
+  if constexpr (kStage) {
+    // The six density sub-blocks D_ab, D_cd, D_ac, D_ad, D_bc, D_bd, each a
+    // row-major block with row stride ldb: staged once in the scratch the
+    // transforms no longer need (Yh, R0, R1, F) when they fit there, else read
+    // from D in place (row stride N).
+    const Real *Db[6];
+    int ldb[6];
+    const int r0[6] = {fa, fc, fa, fa, fb, fb}, c0[6] = {fb, fd, fc, fd, fc, fd};
+    const int nr[6] = {na, nc, na, na, nb, nb}, ncl[6] = {nb, nd, nc, nd, nc, nd};
+    const int nstage = nab + ncd + (na + nb) * (nc + nd);
+    if (nstage <= nhab * ncd + 2 * nhL + L + 1) {
+      Real *Ds = Yh;
+      int off = 0;
+      for (int k = 0; k < 6; ++k) {
+        Db[k] = Ds + off;
+        ldb[k] = ncl[k];
+        const int nk = nr[k] * ncl[k];
+        for (int i = gl; i < nk; i += G) {
+          const int r = i / ncl[k], c = i - r * ncl[k];
+          Ds[off + i] = Dm[(size_t)(r0[k] + r) * N + c0[k] + c];
+        }
+        off += nk;
       }
-      off += nk;
+      group_sync(gmask, G);
+    } else {
+      for (int k = 0; k < 6; ++k) {
+        Db[k] = Dm + (size_t)r0[k] * N + c0[k];
+        ldb[k] = N;
+      }
     }
-    group_sync(gmask, G);
+    // sum_{i < no, j < ni} x[i so + j si] y[i ldy + j] over two independent
+    // chains (even / odd j)
+    auto dot2d = [](const Real *x, int so, int si, const Real *y, int ldy, int no, int ni) -> Real {
+      Real s0 = Real(0), s1 = Real(0);
+      for (int i = 0; i < no; ++i, x += so, y += ldy) {
+        int j = 0;
+        for (; j + 1 < ni; j += 2) {
+          s0 = fma(x[j * si], y[j], s0);
+          s1 = fma(x[(j + 1) * si], y[j + 1], s1);
+        }
+        if (j < ni) s0 = fma(x[j * si], y[j], s0);
+      }
+      return s0 + s1;
+    };
+    // J outputs are o < n2, K outputs n2 <= o < n6: only the built parts
+    const int o0 = (a.parts & 1) ? 0 : n2, o1 = (a.parts & 2) ? n6 : n2;
+    const int scd = ncd, sbcd = nb * ncd;  // eri strides of the b and a indices
+    for (int o = o0 + gl; o < o1; o += G) {
+      Real s;
+      double *dst;
+      if (o < n1) {  // J_ab += (ab|cd) D_cd
+        const int ia = o / nb, ib = o - ia * nb;
+        s = fac2 * dot2d(eri + (size_t)o * ncd, nd, 1, Db[1], ldb[1], nc, nd);
+        dst = mv.J + (size_t)(fa + ia) * N + fb + ib;
+      } else if (o < n2) {  // J_cd += (ab|cd) D_ab
+        const int k = o - n1, ic = k / nd, id = k - ic * nd;
+        s = fac2 * dot2d(eri + k, sbcd, scd, Db[0], ldb[0], na, nb);
+        dst = mv.J + (size_t)(fc + ic) * N + fd + id;
+      } else if (o < n3) {  // K_ac += (ab|cd) D_bd
+        const int k = o - n2, ia = k / nc, ic = k - ia * nc;
+        s = fac * dot2d(eri + (size_t)ia * sbcd + ic * nd, scd, 1, Db[5], ldb[5], nb, nd);
+        dst = mv.K + (size_t)(fa + ia) * N + fc + ic;
+      } else if (o < n4) {  // K_ad += (ab|cd) D_bc
+        const int k = o - n3, ia = k / nd, id = k - ia * nd;
+        s = fac * dot2d(eri + (size_t)ia * sbcd + id, scd, nd, Db[4], ldb[4], nb, nc);
+        dst = mv.K + (size_t)(fa + ia) * N + fd + id;
+      } else if (o < n5) {  // K_bc += (ab|cd) D_ad
+        const int k = o - n4, ib = k / nc, ic = k - ib * nc;
+        s = fac * dot2d(eri + (size_t)ib * scd + ic * nd, sbcd, 1, Db[3], ldb[3], na, nd);
+        dst = mv.K + (size_t)(fb + ib) * N + fc + ic;
+      } else {  // K_bd += (ab|cd) D_ac
+        const int k = o - n5, ib = k / nd, id = k - ib * nd;
+        s = fac * dot2d(eri + (size_t)ib * scd + id, sbcd, nd, Db[2], ldb[2], na, nc);
+        dst = mv.K + (size_t)(fb + ib) * N + fd + id;
+      }
+      if constexpr (F32)
+        atomicAdd(dst, f2d_any(s));
+      else
+        atomicAdd(dst, s);
+    }
   } else {
-    for (int k = 0; k < 6; ++k) {
-      Db[k] = Dm + (size_t)r0[k] * N + c0[k];
-      ldb[k] = N;
-    }
-  }
-  // sum_{i < no, j < ni} x[i so + j si] y[i ldy + j] over two independent
-  // chains (even / odd j)
-  auto dot2d = [](const Real *x, int so, int si, const Real *y, int ldy, int no, int ni) -> Real {
-    Real s0 = Real(0), s1 = Real(0);
-    for (int i = 0; i < no; ++i, x += so, y += ldy) {
-      int j = 0;
-      for (; j + 1 < ni; j += 2) {
-        s0 = fma(x[j * si], y[j], s0);
-        s1 = fma(x[(j + 1) * si], y[j + 1], s1);
+    // sum_m x(m) y(m) over two independent chains (even / odd m)
+    auto dot2 = [](int n, auto &&xy) -> Real {
+      Real s0 = Real(0), s1 = Real(0), x, y;
+      int m = 0;
+      for (; m + 1 < n; m += 2) {
+        xy(m, x, y);
+        s0 = fma(x, y, s0);
+        xy(m + 1, x, y);
+        s1 = fma(x, y, s1);
       }
-      if (j < ni) s0 = fma(x[j * si], y[j], s0);
+      if (m < n) {
+        xy(m, x, y);
+        s0 = fma(x, y, s0);
+      }
+      return s0 + s1;
+    };
+    // J outputs are o < n2, K outputs n2 <= o < n6: only the built parts
+    const int o0 = (a.parts & 1) ? 0 : n2, o1 = (a.parts & 2) ? n6 : n2;
+    for (int o = o0 + gl; o < o1; o += G) {
+      Real s;
+      double *dst;
+      if (o < n1) {  // J_ab += (ab|cd) D_cd
+        const int ia = o / nb, ib = o - ia * nb;
+        const Real *e = eri + (size_t)o * ncd;
+        s = dot2(ncd, [&](int m, Real &x, Real &y) {
+          const int ic = m / nd, id = m - ic * nd;
+          x = e[m];
+          y = Dm[(size_t)(fc + ic) * N + fd + id];
+        });
+        dst = mv.J + (size_t)(fa + ia) * N + fb + ib;
+        s *= fac2;
+      } else if (o < n2) {  // J_cd += (ab|cd) D_ab
+        const int k = o - n1, ic = k / nd, id = k - ic * nd;
+        s = dot2(nab, [&](int m, Real &x, Real &y) {
+          const int ia = m / nb, ib = m - ia * nb;
+          x = eri[(size_t)m * ncd + k];
+          y = Dm[(size_t)(fa + ia) * N + fb + ib];
+        });
+        dst = mv.J + (size_t)(fc + ic) * N + fd + id;
+        s *= fac2;
+      } else if (o < n3) {  // K_ac += (ab|cd) D_bd
+        const int k = o - n2, ia = k / nc, ic = k - ia * nc;
+        s = dot2(nb * nd, [&](int m, Real &x, Real &y) {
+          const int ib = m / nd, id = m - ib * nd;
+          x = eri[((ia * nb + ib) * nc + ic) * nd + id];
+          y = Dm[(size_t)(fb + ib) * N + fd + id];
+        });
+        dst = mv.K + (size_t)(fa + ia) * N + fc + ic;
+        s *= fac;
+      } else if (o < n4) {  // K_ad += (ab|cd) D_bc
+        const int k = o - n3, ia = k / nd, id = k - ia * nd;
+        s = dot2(nb * nc, [&](int m, Real &x, Real &y) {
+          const int ib = m / nc, ic = m - ib * nc;
+          x = eri[((ia * nb + ib) * nc + ic) * nd + id];
+          y = Dm[(size_t)(fb + ib) * N + fc + ic];
+        });
+        dst = mv.K + (size_t)(fa + ia) * N + fd + id;
+        s *= fac;
+      } else if (o < n5) {  // K_bc += (ab|cd) D_ad
+        const int k = o - n4, ib = k / nc, ic = k - ib * nc;
+        s = dot2(na * nd, [&](int m, Real &x, Real &y) {
+          const int ia = m / nd, id = m - ia * nd;
+          x = eri[((ia * nb + ib) * nc + ic) * nd + id];
+          y = Dm[(size_t)(fa + ia) * N + fd + id];
+        });
+        dst = mv.K + (size_t)(fb + ib) * N + fc + ic;
+        s *= fac;
+      } else {  // K_bd += (ab|cd) D_ac
+        const int k = o - n5, ib = k / nd, id = k - ib * nd;
+        s = dot2(na * nc, [&](int m, Real &x, Real &y) {
+          const int ia = m / nc, ic = m - ia * nc;
+          x = eri[((ia * nb + ib) * nc + ic) * nd + id];
+          y = Dm[(size_t)(fa + ia) * N + fc + ic];
+        });
+        dst = mv.K + (size_t)(fb + ib) * N + fd + id;
+        s *= fac;
+      }
+      if constexpr (F32)
+        atomicAdd(dst, f2d_any(s));
+      else
+        atomicAdd(dst, s);
     }
-    return s0 + s1;
-  };
-  // J outputs are o < n2, K outputs n2 <= o < n6: only the built parts
-  const int o0 = (a.parts & 1) ? 0 : n2, o1 = (a.parts & 2) ? n6 : n2;
-  const int scd = ncd, sbcd = nb * ncd;  // eri strides of the b and a indices
-  for (int o = o0 + gl; o < o1; o += G) {
-    Real s;
-    double *dst;
-    if (o < n1) {  // J_ab += (ab|cd) D_cd
-      const int ia = o / nb, ib = o - ia * nb;
-      s = fac2 * dot2d(eri + (size_t)o * ncd, nd, 1, Db[1], ldb[1], nc, nd);
-      dst = mv.J + (size_t)(fa + ia) * N + fb + ib;
-    } else if (o < n2) {  // J_cd += (ab|cd) D_ab
-      const int k = o - n1, ic = k / nd, id = k - ic * nd;
-      s = fac2 * dot2d(eri + k, sbcd, scd, Db[0], ldb[0], na, nb);
-      dst = mv.J + (size_t)(fc + ic) * N + fd + id;
-    } else if (o < n3) {  // K_ac += (ab|cd) D_bd
-      const int k = o - n2, ia = k / nc, ic = k - ia * nc;
-      s = fac * dot2d(eri + (size_t)ia * sbcd + ic * nd, scd, 1, Db[5], ldb[5], nb, nd);
-      dst = mv.K + (size_t)(fa + ia) * N + fc + ic;
-    } else if (o < n4) {  // K_ad += (ab|cd) D_bc
-      const int k = o - n3, ia = k / nd, id = k - ia * nd;
-      s = fac * dot2d(eri + (size_t)ia * sbcd + id, scd, nd, Db[4], ldb[4], nb, nc);
-      dst = mv.K + (size_t)(fa + ia) * N + fd + id;
-    } else if (o < n5) {  // K_bc += (ab|cd) D_ad
-      const int k = o - n4, ib = k / nc, ic = k - ib * nc;
-      s = fac * dot2d(eri + (size_t)ib * scd + ic * nd, sbcd, 1, Db[3], ldb[3], na, nd);
-      dst = mv.K + (size_t)(fb + ib) * N + fc + ic;
-    } else {  // K_bd += (ab|cd) D_ac
-      const int k = o - n5, ib = k / nd, id = k - ib * nd;
-      s = fac * dot2d(eri + (size_t)ib * scd + id, sbcd, nd, Db[2], ldb[2], na, nc);
-      dst = mv.K + (size_t)(fb + ib) * N + fd + id;
-    }
-    if constexpr (F32)
-      atomicAdd(dst, f2d_any(s));
-    else
-      atomicAdd(dst, s);
   }
   group_sync(gmask, G);
 }
