@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -198,10 +199,25 @@ def write_traffic(csv_path: str):
     return d
 
 
+_CODE_TOKENS = re.compile(r"//[^\n]*|/\*.*?\*/|'(?:\\.|[^\\'\n])*'|\"(?:\\.|[^\\\"\n])*\"", re.S)
+
+
+def code_only(src: str) -> str:
+    """C/C++/CUDA source with its comments removed and whitespace runs
+    collapsed (string and character literals kept as they are)."""
+    out = _CODE_TOKENS.sub(lambda m: " " if m.group(0)[0] == "/" else m.group(0), src)
+    return " ".join(out.split())
+
+
 def kernel_hash():
+    """SHA-256 over the library's sources (csrc/, by file name) with comments
+    and layout removed: the key of the traffic profile, which holds as long
+    as the compiled code is the same."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2407_21445_gb300", "csrc"))):
-        h.update(open(os.path.join(ROOT, "paper_2407_21445_gb300", "csrc", f), "rb").read())
+    d = os.path.join(ROOT, "paper_2407_21445_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode() + b"\0")
+        h.update(code_only(open(os.path.join(d, f), encoding="utf-8").read()).encode())
     return h.hexdigest()
 
 

@@ -1,7 +1,9 @@
 // Per-class register kernels: one thread owns one contracted shell quartet
-// of a fixed angular-momentum class (la lb|lc ld) with total L <= 3; every
-// loop has a compile-time trip count and every intermediate (Boys seeds,
-// Hermite integrals R, half-transformed Y, contracted ERIs) is a register.
+// of a fixed angular-momentum class (la lb|lc ld) with total L <= 4 (k_reg;
+// FP32 quartets of total L = 5 and (dd|pp) in k_reg32); every loop has a
+// compile-time trip count and the intermediates (Boys seeds, Hermite
+// integrals R, half-transformed Y) are registers, the contracted ERIs too
+// except in the largest classes, which keep them in per-thread shared memory.
 // Same McMurchie-Davidson steps and digestion as the group kernel in
 // kernels_jk.cu (Sec. 4.1 Eqs. MD def, EabP def1-3; Sec. 3.2 digestion).
 #pragma once
