@@ -49,3 +49,15 @@ def test_fma_probe_compiles_for_sm103a(tmp_path):
     for shape in ("m8n8k4.row.col.f64", "m16n8k8.row.col.f32.tf32", "m16n8k16.row.col.f32.bf16",
                   "m16n8k32.row.col.s32.s8"):
         assert shape in bench.FMA_PROBE_SRC
+
+
+def test_kernel_hash_ignores_comments_and_layout():
+    """The traffic profile's key changes with the code, not with comments or
+    layout; string literals that contain comment markers are code."""
+    import bench
+    a = 'int a; // note\n/* block\n comment */ const char *s = "x//y/*z*/";\n'
+    b = 'int   a;\nconst char *s = "x//y/*z*/";   // other note\n'
+    c = 'int a; const char *s = "x//y*/";\n'
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only(a) != bench.code_only(c)
+    assert '"x//y/*z*/"' in bench.code_only(a)
