@@ -5,6 +5,7 @@ import pytest
 
 import molgen
 import oracle
+from oracle import scf as oracle_scf
 
 pytestmark = pytest.mark.gpu
 
@@ -18,46 +19,6 @@ def env():
     return torch, scf
 
 
-def oracle_scf(basis, Z, xyz, nocc, tau, D0, iters=200):
-    """Plain CPU RHF on oracle integrals (Sec. 2.2), Pulay DIIS."""
-    S = oracle.overlap(basis)
-    h = oracle.kinetic(basis) + oracle.nuclear(basis, Z, xyz)
-    s, U = np.linalg.eigh(S)
-    X = U[:, s > 1e-7] / np.sqrt(s[s > 1e-7])
-    from paper_2407_21445_gb300.scf import nuclear_repulsion
-    enuc = nuclear_repulsion(Z, xyz)
-    D = D0
-    Fs, Es = [], []
-    e_prev = None
-    for it in range(iters):
-        J, K = oracle.jk(basis, D, tau)
-        F = h + J - 0.5 * K
-        E = 0.5 * np.sum(D * (h + F)) + enuc
-        err = X.T @ (F @ D @ S - S @ D @ F) @ X
-        if e_prev is not None and abs(E - e_prev) < 1e-10 and np.abs(err).max() < 1e-7:
-            return E
-        e_prev = E
-        Fs.append(F)
-        Es.append(err)
-        Fs, Es = Fs[-8:], Es[-8:]
-        n = len(Fs)
-        Fx = F
-        if n >= 2:
-            B = -np.ones((n + 1, n + 1))
-            B[n, n] = 0
-            for i in range(n):
-                for j in range(n):
-                    B[i, j] = np.sum(Es[i] * Es[j])
-            rhs = np.zeros(n + 1)
-            rhs[n] = -1
-            c = np.linalg.solve(B, rhs)
-            Fx = sum(c[i] * Fs[i] for i in range(n))
-        e, C = np.linalg.eigh(X.T @ Fx @ X)
-        C = X @ C
-        D = 2 * C[:, :nocc] @ C[:, :nocc].T
-    raise AssertionError("oracle SCF did not converge")
-
-
 def test_scf_water_trimer_guess_independent_and_oracle(env):
     torch, scf = env
     p = molgen.problem(0)
@@ -69,7 +30,7 @@ def test_scf_water_trimer_guess_independent_and_oracle(env):
     assert abs(r_core.energy - r_sad.energy) < 1e-8
     assert r_sad.iterations <= r_core.iterations
     D0 = rhf.core_guess().cpu().numpy()
-    e_or = oracle_scf(p.basis, Z, xyz, rhf.nocc, p.tau, D0)
+    e_or = oracle_scf.rhf(p.basis, Z, xyz, rhf.nocc, tau=p.tau, D0=D0)["energy"]
     assert abs(r_sad.energy - e_or) < 1e-8, (r_sad.energy, e_or)
 
 
