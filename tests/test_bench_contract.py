@@ -61,3 +61,17 @@ def test_kernel_hash_ignores_comments_and_layout():
     assert bench.code_only(a) == bench.code_only(b)
     assert bench.code_only(a) != bench.code_only(c)
     assert '"x//y/*z*/"' in bench.code_only(a)
+
+
+def test_cpu_baseline_counts_sampled_work_only():
+    """The CPU baseline times the oracle over a sample of outer shell pairs
+    and leaves the per-call setup (Schwarz factors of all pairs) out of the
+    rate; on the water trimer the sample is the whole loop (stride 1)."""
+    import bench
+    import molgen
+    import oracle
+    p = molgen.problem(0)
+    r = bench.cpu_baseline(p, target_s=0.2)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] == oracle.threads()
+    assert "not counted" in r["sample"]
+    assert bench.oracle_setup_seconds(p) > 0
